@@ -1,0 +1,245 @@
+"""Plain CPU oracle: Euler characteristic curve by explicit cell enumeration.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring): not importable from the
+product path, never called by the CUDA library.
+
+What it computes, and the passage each step follows (Heiss & Wagner,
+"Streaming Algorithm for Euler Characteristic Curves of Multidimensional
+Images"):
+
+* Cells (Sec. 2, "Cubical Cell"): a product of d factors, each a unit interval
+  [a, a+1] or a singleton {b}; dim = number of interval factors.
+* The image complex (Sec. 2, "Consecutive Thresholded Images as Sublevel Set
+  Filtrations"): voxel i = (i_1..i_d) is the top cell prod_k [i_k - 1, i_k]
+  (here shifted to 0-based: voxel i covers prod_k [i_k, i_k + 1]); the complex is
+  all voxels with all their faces.
+* Filtration value (Sec. 2, "Sublevel Set Filtration", the extension f~): a voxel
+  carries its gray value; any other cell the MINIMUM over the voxels that
+  contain it. This is convention "V", the paper's.
+* Euler characteristic (Sec. 2, "Euler Characteristic"): chi = sum_k (-1)^k n_k.
+* VCEC and curve (Sec. 3, "Tracking the Changes"): a_t = chi(K_t) - chi(K_{t-1})
+  with chi(empty) = 0, and the curve is the running sum (a_0, a_0 + a_1, ...).
+  a_t is therefore the signed count of cells whose filtration value equals t.
+* Integer range (Sec. 3, "Range of Values"): thresholds t in {0..m-1}.
+* Other ranges (Sec. 3, "Other Ranges of Gray Values"): for float images the
+  VCEC is keyed by the value itself (the paper's hash map); output is the list
+  of (t, chi(K_t)) at the values t where a_t != 0, ascending.
+
+Convention "T" is the alternative the same section names in a footnote: the
+dual complex, voxels as vertices, lower-star filtration. A cell is a box of
+2^k voxel centres spanned by unit steps and takes the MAXIMUM of its vertices.
+
+Nothing here uses neighbour masks, tie-breaks, or the per-voxel block
+decomposition of Sec. 3 ("Tracking the Changes", Algorithm 1). Library
+primitives used as steps: numpy minimum/maximum, bincount, unique, cumsum.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+# Stands for the value +inf of voxels outside the image (integer images).
+SENTINEL_INT = np.iinfo(np.int32).max
+
+
+def _exact_values(img: np.ndarray):
+    """Return (values, sentinel) in a type where min/max and equality are exact.
+
+    Unsigned/signed integers up to 31 bits go to int32 (sentinel 2^31-1 is
+    above every representable input value); floats go to float64 with -0.0
+    normalised to +0.0 (IEEE equality already treats them as one value; the
+    normalisation only fixes which bit pattern represents it) and +inf as the
+    sentinel. NaN and +-inf inputs are rejected: the paper reserves infinity for
+    the collar of outside voxels (Sec. 4, limitations).
+    """
+    if img.dtype.kind in "ui":
+        if img.size and (int(img.max()) >= SENTINEL_INT or int(img.min()) < 0):
+            raise ValueError("integer values must lie in [0, 2^31 - 1)")
+        return img.astype(np.int32), SENTINEL_INT
+    if img.dtype.kind == "f":
+        v = img.astype(np.float64) + 0.0
+        if not np.all(np.isfinite(v)):
+            raise ValueError("NaN or infinite values are not gray values")
+        return v, np.inf
+    raise TypeError(f"unsupported dtype {img.dtype}")
+
+
+def _sl(a: np.ndarray, axis: int, lo: int, hi: int) -> np.ndarray:
+    idx = [slice(None)] * a.ndim
+    idx[axis] = slice(lo, hi)
+    return a[tuple(idx)]
+
+
+def cells_V(img: np.ndarray, lo: int = 0, hi: int | None = None):
+    """Yield (dim, values) for every cell type of the paper's complex (conv. V).
+
+    A cell type picks, per axis k, an interval [a, a+1] with 0 <= a < n_k or a
+    singleton {b} with 0 <= b <= n_k. The voxels containing such a cell are, per
+    axis, {a} for an interval and {b-1, b} intersected with [0, n_k) for a
+    singleton. Its value is the minimum over those voxels. ``values`` holds that
+    minimum for every cell of the type (one array entry per cell).
+
+    ``lo``/``hi`` restrict the axis-0 coordinate (a or b) of the enumerated
+    cells to [lo, hi); the default enumerates all cells. Disjoint ranges
+    partition the cell set, which is what the chunked streaming of Sec. 3
+    ("Streaming") relies on.
+    """
+    n0 = img.shape[0]
+    if hi is None:
+        hi = n0 + 1
+    lo, hi = max(lo, 0), min(hi, n0 + 1)
+    if img.size == 0 or lo >= hi:
+        return
+    # Padded coordinate p along every axis stands for voxel p - 1; padded
+    # entries outside the image hold the sentinel (+inf). Along axis 0 only
+    # padded rows [lo, hi + 1) are needed.
+    p_lo, p_hi = lo, min(hi + 1, n0 + 2)
+    v_lo, v_hi = max(p_lo - 1, 0), min(p_hi - 1, n0)
+    vals, sentinel = _exact_values(img[v_lo:v_hi])
+    pad = [(1 if p_lo == 0 else 0, 1 if p_hi == n0 + 2 else 0)]
+    pad += [(1, 1)] * (img.ndim - 1)
+    P = np.pad(vals, pad, constant_values=sentinel)
+    for kinds in itertools.product("IS", repeat=img.ndim):
+        A = P
+        for axis, kind in enumerate(kinds):
+            n = img.shape[axis]
+            if axis == 0:
+                a_hi, b_hi = min(hi, n), min(hi, n + 1)
+                if kind == "I":          # a in [lo, a_hi): padded a + 1
+                    A = _sl(A, 0, lo + 1 - p_lo, a_hi + 1 - p_lo)
+                else:                    # b in [lo, b_hi): padded b and b + 1
+                    A = np.minimum(_sl(A, 0, lo - p_lo, b_hi - p_lo),
+                                   _sl(A, 0, lo + 1 - p_lo, b_hi + 1 - p_lo))
+            elif kind == "I":            # a in [0, n): padded a + 1
+                A = _sl(A, axis, 1, n + 1)
+            else:                        # b in [0, n]: padded b and b + 1
+                A = np.minimum(_sl(A, axis, 0, n + 1), _sl(A, axis, 1, n + 2))
+        if A.size == 0:
+            continue
+        # every cell contains at least one voxel of the image
+        assert not np.any(A == sentinel)
+        yield kinds.count("I"), A
+
+
+def cells_T(img: np.ndarray, lo: int = 0, hi: int | None = None):
+    """Yield (dim, values) for every cell type of the dual complex (conv. T).
+
+    Voxel centres are the vertices. A cell type picks, per axis, a point a
+    (0 <= a < n_k) or an edge [a, a+1] (0 <= a < n_k - 1); the cell's vertices
+    are all voxels with coordinate a (point) or a, a+1 (edge) on each axis, and
+    its value is their MAXIMUM (lower-star filtration). ``lo``/``hi`` restrict
+    the axis-0 coordinate a to [lo, hi).
+    """
+    n0 = img.shape[0]
+    if hi is None:
+        hi = n0
+    lo, hi = max(lo, 0), min(hi, n0)
+    if img.size == 0 or lo >= hi:
+        return
+    vals, _ = _exact_values(img[lo:min(hi + 1, n0)])
+    for kinds in itertools.product("PE", repeat=img.ndim):
+        A = vals
+        for axis, kind in enumerate(kinds):
+            n = A.shape[axis]
+            if axis == 0:
+                if kind == "P":          # a in [lo, hi)
+                    A = _sl(A, 0, 0, hi - lo)
+                else:                    # a in [lo, min(hi, n0 - 1)): a, a + 1
+                    e_hi = min(hi, n0 - 1)
+                    A = np.maximum(_sl(A, 0, 0, e_hi - lo),
+                                   _sl(A, 0, 1, e_hi - lo + 1))
+            elif kind == "E":
+                A = np.maximum(_sl(A, axis, 0, n - 1), _sl(A, axis, 1, n))
+        if A.size == 0:
+            continue
+        yield kinds.count("E"), A
+
+
+def _cells(img, convention, lo=0, hi=None):
+    if convention == "V":
+        return cells_V(img, lo, hi)
+    if convention == "T":
+        return cells_T(img, lo, hi)
+    raise ValueError(f"unknown convention {convention!r}")
+
+
+def vcec_int(img: np.ndarray, bins: int, convention: str = "V") -> np.ndarray:
+    """VCEC a[0..bins-1] of an integer image: a_t = sum over cells with value t
+    of (-1)^dim (Sec. 2 "Euler Characteristic" with Sec. 3 "Tracking the
+    Changes"). Values >= bins raise ValueError (no clamping)."""
+    return vcec_int_zrange(img, bins, 0, None, convention)
+
+
+def vcec_int_zrange(img: np.ndarray, bins: int, lo: int, hi: int | None,
+                    convention: str = "V") -> np.ndarray:
+    """VCEC restricted to the cells whose axis-0 coordinate lies in [lo, hi).
+
+    Summing this over a partition of the axis-0 coordinates gives
+    ``vcec_int`` of the whole image: the chunk decomposition of Sec. 3
+    ("Streaming", "Processing one Chunk").
+    """
+    if img.dtype.kind not in "ui":
+        raise TypeError("integer image expected")
+    a = np.zeros(bins, dtype=np.int64)
+    for dim, A in _cells(img, convention, lo, hi):
+        flat = A.ravel()
+        if flat.size and int(flat.max()) >= bins:
+            raise ValueError("a gray value is >= bins")
+        a += (-1) ** dim * np.bincount(flat, minlength=bins).astype(np.int64)
+    return a
+
+
+def ecc_from_vcec(a: np.ndarray) -> np.ndarray:
+    """Curve (a_0, a_0 + a_1, ..., sum_t a_t) (Sec. 3, "Post-Processing")."""
+    return np.cumsum(np.asarray(a, dtype=np.int64), dtype=np.int64)
+
+
+def ecc_int(img: np.ndarray, bins: int, convention: str = "V") -> np.ndarray:
+    """Euler characteristic curve chi(K_t), t = 0..bins-1, of an integer image."""
+    return ecc_from_vcec(vcec_int(img, bins, convention))
+
+
+def ecc_pairs_float(img: np.ndarray, convention: str = "V"):
+    """Float image: (thresholds, chi) at every value t with a_t != 0, ascending.
+
+    The VCEC is keyed by the value itself (Sec. 3, "Other Ranges of Gray
+    Values", the hash-map variant); chi(K_t) at a listed t is the running sum
+    of a over all values <= t. Between two listed thresholds the curve is
+    constant. Returns (float32 array, int64 array).
+    """
+    keys, weights = [], []
+    for dim, A in _cells(img, convention):
+        u, c = np.unique(A.ravel(), return_counts=True)
+        keys.append(u)
+        weights.append((-1) ** dim * c.astype(np.int64))
+    if not keys:
+        return np.zeros(0, np.float32), np.zeros(0, np.int64)
+    k = np.concatenate(keys)
+    w = np.concatenate(weights)
+    order = np.argsort(k, kind="stable")
+    k, w = k[order], w[order]
+    starts = np.flatnonzero(np.r_[True, k[1:] != k[:-1]])
+    a = np.add.reduceat(w, starts)
+    t = k[starts]
+    keep = a != 0
+    return t[keep].astype(np.float32), np.cumsum(a[keep], dtype=np.int64)
+
+
+def cell_counts(img_shape, convention: str = "V"):
+    """n_k, the number of k-dimensional cells of the full complex of an image
+    of this shape (every cell present, i.e. the threshold above all values)."""
+    d = len(img_shape)
+    n = np.zeros(d + 1, dtype=np.int64)
+    if any(s == 0 for s in img_shape):
+        return n
+    for kinds in itertools.product((0, 1), repeat=d):
+        # 1 = interval (V) / edge (T) factor
+        cnt = 1
+        for s, k in zip(img_shape, kinds):
+            if convention == "V":
+                cnt *= s if k else s + 1
+            else:
+                cnt *= s - 1 if k else s
+        n[sum(kinds)] += cnt
+    return n

@@ -1,0 +1,314 @@
+"""Benchmark: Euler characteristic curve of a 512^3 uint8 image on one GB300.
+
+Workload (one "step"): the whole hot path -- per-voxel change of Algorithm 1
+(contribution kernel, block-private histogram, int64 merge) and the prefix
+scan -- on a 512 x 512 x 512 uint8 image (seeded white noise, Gaussian
+sigma = 4, requantised to 0..255; 256 thresholds), resident in HBM.
+
+  value      Gvoxel/s from CUDA events around each step on the launching
+             stream; L2 is flushed (256 MiB write) between steps, outside
+             the timed events.
+  e2e        same metric through ecc_compute() with the image in pinned host
+             memory: host->device copy, kernels, device->host curve, all timed.
+  roofline   contribution kernel: algorithmic bytes (1 byte per voxel read
+             once + 8 bytes per bin written) / its event-timed duration,
+             against the measured HBM copy bandwidth.
+  cpu_baseline  the CPU oracle on a bounded slab of the same image.
+
+N > 1 (torchrun): replicas, one image per rank, weak scaling; value is the
+voxels of all ranks / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SHAPE = (512, 512, 512)
+BINS = 256
+SIGMA = 4.0
+METRIC = "ECC Gvoxel/s & % HBM roofline; batched vs per-image launch; p50/p99 latency"
+WORKLOAD = "3D 512x512x512 uint8, seeded white noise * Gaussian(sigma=4) requantised 0..255, 256 bins, HBM-resident"
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(
+                    ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                     "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                    timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for name, v in zip(names, s[4:8]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+def make_image(seed_offset: int = 1):
+    from paper_1705_02045_gb300 import synth
+    return synth.smooth_u8(SHAPE, SIGMA, synth.SEED_BASE + seed_offset)
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(img, seconds: float = 15.0):
+    """The oracle, as it stands, on a bounded slab of planes of the image:
+    the cells whose axis-0 coordinate lies in [0, k), k grown until the
+    run takes about `seconds`."""
+    import oracle
+    k, spent, voxels = 1, 0.0, 0
+    total_t, total_v = 0.0, 0
+    while total_t < seconds and k <= img.shape[0]:
+        t0 = time.perf_counter()
+        oracle.vcec_int_zrange(img, BINS, 0, k, "V")
+        dt = time.perf_counter() - t0
+        total_t += dt
+        total_v += k * img.shape[1] * img.shape[2]
+        k *= 2
+    return {"value": total_v / total_t / 1e9, "unit": "Gvoxel/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"cells of planes [0, k) of the same 512^3 image for k = 1, 2, 4, ... "
+                      f"until {seconds:.0f} s: {total_v} voxels in {total_t:.1f} s "
+                      "(numpy, single thread)"}
+
+
+def run_reference(args, world, rank):
+    """--impl reference: the CPU oracle, timed on this host, rank 0 only."""
+    if rank != 0:
+        return
+    img = make_image()
+    budget = 150.0
+    n_steps = args.steps + args.warmup
+    per_step = max(0.05, budget / max(n_steps, 1))
+    # planes per step so that one step takes about per_step seconds
+    import oracle
+    t0 = time.perf_counter()
+    oracle.vcec_int_zrange(img, BINS, 0, 1, "V")
+    one = max(time.perf_counter() - t0, 1e-3)
+    k = int(max(1, min(SHAPE[0], per_step / one)))
+    for i in range(args.warmup):
+        oracle.vcec_int_zrange(img, BINS, 0, k, "V")
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        lo = (i * k) % SHAPE[0]
+        oracle.vcec_int_zrange(img, BINS, lo, min(lo + k, SHAPE[0] + 1), "V")
+    dt = time.perf_counter() - t0
+    vox = args.steps * k * SHAPE[1] * SHAPE[2]
+    value = vox / dt / 1e9
+    line = {"metric": METRIC, "value": value, "unit": "Gvoxel/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / max(args.steps, 1) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD + f"; each step = cells of {k} plane(s)",
+                       "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": "Gvoxel/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{k} planes of 512x512 per step"},
+            "e2e": {"value": value, "unit": "Gvoxel/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    args = ap.parse_args()
+    world, rank, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    from paper_1705_02045_gb300 import ecc
+
+    if args.warmup < 3:
+        args.warmup = 3
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    ecc.load()
+    h = ecc.ecc_create(device=local)
+
+    img = make_image(1 + rank)
+    nvox = img.size
+    d_img = torch.from_numpy(img).cuda()
+    d_curve = torch.empty(BINS, dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+
+    # correctness guard on this very input: top of the curve is 1 (box contractible)
+    ecc.ecc_compute_device(h, d_img, BINS, d_curve, stream=stream)
+    stream.synchronize()
+    assert int(d_curve[-1].item()) == 1
+
+    for _ in range(args.warmup):
+        ecc.ecc_compute_device(h, d_img, BINS, d_curve, stream=stream)
+    stream.synchronize()
+
+    ecc.ecc_set_profiling(h, True)
+    ecc.ecc_profile_read(h)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches0 = ecc.ecc_launch_count(h)
+    _barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        t_wall0 = time.perf_counter()
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                starts[i].record(stream)
+            ecc.ecc_compute_device(h, d_img, BINS, d_curve, stream=stream)
+            ends[i].record(stream)
+        stream.synchronize()
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+        if t_wall < 1.5:
+            time.sleep(0.0)
+    _barrier(world)
+    launches = ecc.ecc_launch_count(h) - launches0
+    step_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
+    contrib_ms, n_rec = ecc.ecc_profile_read(h)
+    contrib_ms /= max(n_rec, 1)
+    ecc.ecc_set_profiling(h, False)
+    step_ms_max = _max_over_ranks(step_ms, world)
+    value = world * nvox / (step_ms_max * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (the contribution kernel)
+    peak, peak_kind = measured_peak_hbm()
+    alg_bytes = nvox * 1 + BINS * 8
+    achieved = alg_bytes / (contrib_ms * 1e-3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        try:
+            traffic = json.load(open(tfile)).get("contrib_512cube_u8")
+        except Exception:
+            traffic = None
+
+    # end to end through the public API with a pinned host image
+    h_img = torch.from_numpy(img).pin_memory()
+    for _ in range(2):
+        ecc.ecc_compute(h, h_img)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        curve = ecc.ecc_compute(h, h_img)
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    assert curve[-1] == 1
+    e2e_s = _max_over_ranks(e2e_s, world)
+    e2e_value = world * nvox / e2e_s / 1e9
+
+    if rank == 0:
+        cs = clocks.summary()
+        line = {
+            "metric": METRIC, "value": value, "unit": "Gvoxel/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms_max,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "global_batch": world, "voxels_per_gpu": nvox,
+                       "bins": BINS, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "256 MiB write between steps, outside the timed events"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "contribution+histogram", "peak_kind": peak_kind,
+                         "kernel_ms": contrib_ms},
+            "e2e": {"value": e2e_value, "unit": "Gvoxel/s", "h2d_bytes_per_step": nvox,
+                    "d2h_bytes_per_step": BINS * 8},
+            "gpu_launches": int(launches),
+            "clocks": cs,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(img)
+        print(json.dumps(line), flush=True)
+    ecc.ecc_destroy(h)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,506 @@
+// Host engine: handle lifetime, validation, and the single-image entry points
+// of the C ABI (include/ecc.h). No C++ exception crosses the ABI: every entry
+// point catches and converts to a status code.
+#include "engine.h"
+
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+namespace ecc {
+
+cudaError_t launch_local_generic(const LocalArgs& a, int num_sms, int64_t* launches);
+
+int set_err(ecc_handle* h, int code, const char* fmt, ...) {
+  if (h) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    h->err = buf;
+  }
+  return code;
+}
+
+int cuda_err(ecc_handle* h, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return ECC_OK;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return set_err(h, ECC_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  }
+  return set_err(h, ECC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+size_t dtype_bytes(int dtype) {
+  switch (dtype) {
+    case kU8: return 1;
+    case kU16: return 2;
+    case kF32: return 4;
+    default: return 0;
+  }
+}
+
+int64_t default_bins(const ecc_handle* h, int dtype) {
+  if (h->cfg.bins > 0) return h->cfg.bins;
+  return dtype == kU8 ? 256 : 65536;
+}
+
+int validate_shape(ecc_handle* h, const int64_t* dims, int ndim, Shape* s) {
+  if (!dims) return set_err(h, ECC_ERR_ARG, "dims is NULL");
+  if (ndim < 1 || ndim > 4) return set_err(h, ECC_ERR_ARG, "ndim %d outside 1..4", ndim);
+  s->ndim = ndim;
+  s->voxels = 1;
+  for (int i = 0; i < ndim; ++i) {
+    if (dims[i] < 0) return set_err(h, ECC_ERR_ARG, "dims[%d] = %lld < 0", i, (long long)dims[i]);
+    if (dims[i] > (int64_t(1) << 40))
+      return set_err(h, ECC_ERR_ARG, "dims[%d] too large", i);
+    s->dims[i] = dims[i];
+    s->voxels *= dims[i];
+  }
+  // kernel view: 4D stays (w, z, y, x); 1D-3D become (z, y, x) with
+  // leading extents 1
+  if (ndim == 4) {
+    s->view = 4;
+    for (int i = 0; i < 4; ++i) s->n[i] = dims[i];
+  } else {
+    s->view = 3;
+    s->n[0] = s->n[1] = s->n[2] = s->n[3] = 1;
+    for (int i = 0; i < ndim; ++i) s->n[3 - ndim + i] = dims[i];
+  }
+  return ECC_OK;
+}
+
+bool is_device_ptr(const ecc_handle* h, const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) &&
+         at.device == h->device;
+}
+
+cudaError_t launch_local(const LocalArgs& a, int num_sms, int64_t* launches) {
+  return launch_local_generic(a, num_sms, launches);
+}
+
+// Largest number of voxel planes (of n[0]) per contribution launch so that no
+// block's int32 shared-memory histogram can overflow: a change is at most 21
+// in magnitude (|G_4| <= 3 * 7), and a launch splits its voxels over at least
+// `blocks` blocks of which none takes more than twice its share.
+static int64_t max_planes_per_launch(const Shape& s, int num_sms) {
+  const int64_t per_plane = s.voxels / std::max<int64_t>(s.n[0], 1);
+  const int64_t budget = (int64_t(1) << 31) / 32 * (int64_t)num_sms / 2;
+  if (per_plane <= 0) return s.n[0];
+  return std::max<int64_t>(1, budget / per_plane);
+}
+
+int enqueue_int(ecc_handle* h, const void* d_img, const Shape& s, int dtype, int64_t bins,
+                long long* d_vcec, long long* d_curve, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(d_vcec, 0, sizeof(long long) * bins, stream);
+  if (e != cudaSuccess) return cuda_err(h, e, "memset vcec");
+  if (s.voxels > 0) {
+    LocalArgs a;
+    a.img = d_img;
+    a.dtype = dtype;
+    a.conv = h->cfg.convention;
+    a.view = s.view;
+    for (int i = 0; i < 4; ++i) a.n[i] = s.n[i];
+    a.bins = bins;
+    a.vcec = d_vcec;
+    a.err = h->errw.as<int>();
+    a.stream = stream;
+    a.w_mem_lo = 0;
+    a.w_mem_hi = a.n[0];
+    const int64_t step = max_planes_per_launch(s, h->num_sms);
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (h->prof_on) {
+      if ((e = cudaEventCreate(&ev0)) || (e = cudaEventCreate(&ev1)) ||
+          (e = cudaEventRecord(ev0, stream)))
+        return cuda_err(h, e, "profiling event");
+    }
+    for (int64_t w = 0; w < a.n[0]; w += step) {
+      a.w_lo = w;
+      a.w_hi = std::min(a.n[0], w + step);
+      int64_t cnt = 0;
+      e = launch_local(a, h->num_sms, &cnt);
+      h->launches += cnt;
+      if (e != cudaSuccess) return cuda_err(h, e, "contribution kernel");
+    }
+    if (h->prof_on) {
+      if ((e = cudaEventRecord(ev1, stream))) return cuda_err(h, e, "profiling event");
+      h->prof_events.emplace_back(ev0, ev1);
+    }
+  }
+  int64_t cnt = 0;
+  e = launch_scan(d_vcec, d_curve, bins, stream, &cnt);
+  h->launches += cnt;
+  if (e != cudaSuccess) return cuda_err(h, e, "scan kernel");
+  return ECC_OK;
+}
+
+int wait_event(ecc_handle* h, cudaEvent_t ev, int64_t timeout_us) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) return ECC_OK;
+    if (e != cudaErrorNotReady) return cuda_err(h, e, "event");
+    const auto dt = std::chrono::duration_cast<std::chrono::microseconds>(
+                        std::chrono::steady_clock::now() - t0).count();
+    if (timeout_us >= 0 && dt >= timeout_us)
+      return set_err(h, ECC_ERR_TIMEOUT, "wait ran out after %lld us", (long long)dt);
+    std::this_thread::sleep_for(std::chrono::microseconds(dt < 1000 ? 5 : 100));
+  }
+}
+
+// Bounded stream synchronisation through an event (5 minutes).
+static int sync_stream(ecc_handle* h, cudaStream_t s) {
+  cudaEvent_t ev;
+  cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_err(h, e, "event create");
+  e = cudaEventRecord(ev, s);
+  int rc = e == cudaSuccess ? wait_event(h, ev, 300LL * 1000 * 1000) : cuda_err(h, e, "record");
+  cudaEventDestroy(ev);
+  return rc;
+}
+
+static int read_err_word(ecc_handle* h, cudaStream_t s, int* word) {
+  cudaError_t e = cudaMemcpyAsync(h->h_err, h->errw.p, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_err(h, e, "read error word");
+  int rc = sync_stream(h, s);
+  if (rc) return rc;
+  *word = *h->h_err;
+  return ECC_OK;
+}
+
+static int err_word_status(ecc_handle* h, int word) {
+  if (word & kErrValue)
+    return set_err(h, ECC_ERR_VALUE, "a value is >= bins, or a float is NaN/Inf");
+  if (word & kErrOverflow)
+    return set_err(h, ECC_ERR_CUDA, "internal capacity exceeded (error word %d)", word);
+  return ECC_OK;
+}
+
+static float key_to_float(uint32_t k) {
+  const uint32_t b = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
+  float f;
+  std::memcpy(&f, &b, 4);
+  return f;
+}
+
+static int compute_float(ecc_handle* h, const void* d_img, const Shape& s, ecc_result* out) {
+  cudaStream_t st = h->stream;
+  const int64_t n = s.voxels;
+  cudaError_t e;
+  if ((e = h->pairs.ensure(sizeof(unsigned long long) * std::max<int64_t>(n, 1))) ||
+      (e = h->pair_count.ensure(sizeof(unsigned long long))) ||
+      (e = h->tmp.ensure(float_tail_tmp_bytes(n))) ||
+      (e = h->out_keys.ensure(sizeof(uint32_t) * std::max<int64_t>(n, 1))) ||
+      (e = h->out_chi.ensure(sizeof(long long) * std::max<int64_t>(n, 1))) ||
+      (e = h->out_count.ensure(sizeof(unsigned long long))))
+    return cuda_err(h, e, "float buffers");
+  if ((e = cudaMemsetAsync(h->pair_count.p, 0, sizeof(unsigned long long), st)))
+    return cuda_err(h, e, "memset");
+  LocalArgs a;
+  a.img = d_img;
+  a.dtype = kF32;
+  a.conv = h->cfg.convention;
+  a.view = s.view;
+  for (int i = 0; i < 4; ++i) a.n[i] = s.n[i];
+  a.w_lo = 0; a.w_hi = a.n[0]; a.w_mem_lo = 0; a.w_mem_hi = a.n[0];
+  a.err = h->errw.as<int>();
+  a.pairs = h->pairs.as<unsigned long long>();
+  a.pair_count = h->pair_count.as<unsigned long long>();
+  a.pair_cap = n;
+  a.stream = st;
+  int64_t cnt = 0;
+  if ((e = launch_local(a, h->num_sms, &cnt))) return cuda_err(h, e, "pairs kernel");
+  h->launches += cnt;
+  unsigned long long npairs = 0;
+  if ((e = cudaMemcpyAsync(&npairs, h->pair_count.p, 8, cudaMemcpyDeviceToHost, st)))
+    return cuda_err(h, e, "copy count");
+  int word = 0;
+  int rc = read_err_word(h, st, &word);
+  if (rc) return rc;
+  if ((rc = err_word_status(h, word))) return rc;
+  cnt = 0;
+  if ((e = launch_float_tail(h->pairs.as<unsigned long long>(), (int64_t)npairs, h->tmp.p,
+                             h->tmp.cap, h->out_keys.as<uint32_t>(), h->out_chi.as<long long>(),
+                             h->out_count.as<unsigned long long>(), st, &cnt)))
+    return cuda_err(h, e, "float tail");
+  h->launches += cnt;
+  unsigned long long k = 0;
+  if ((e = cudaMemcpyAsync(&k, h->out_count.p, 8, cudaMemcpyDeviceToHost, st)))
+    return cuda_err(h, e, "copy count");
+  if ((rc = sync_stream(h, st))) return rc;
+  std::vector<uint32_t> keys(k);
+  out->npairs = (int64_t)k;
+  out->thresholds = static_cast<float*>(std::malloc(sizeof(float) * std::max<uint64_t>(k, 1)));
+  out->chi = static_cast<int64_t*>(std::malloc(sizeof(int64_t) * std::max<uint64_t>(k, 1)));
+  if (!out->thresholds || !out->chi) return set_err(h, ECC_ERR_OOM, "host result");
+  if (k) {
+    if ((e = cudaMemcpyAsync(keys.data(), h->out_keys.p, 4 * k, cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaMemcpyAsync(out->chi, h->out_chi.p, 8 * k, cudaMemcpyDeviceToHost, st)))
+      return cuda_err(h, e, "copy pairs");
+    if ((rc = sync_stream(h, st))) return rc;
+  }
+  for (uint64_t i = 0; i < k; ++i) out->thresholds[i] = key_to_float(keys[i]);
+  return ECC_OK;
+}
+
+}  // namespace ecc
+
+using namespace ecc;
+
+extern "C" {
+
+void ecc_config_default(ecc_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof *c);
+  c->device = 0;
+  c->convention = ECC_CONV_V;
+  c->bins = 0;
+  c->slab_depth = 64;
+  c->ring_bytes = int64_t(4) << 30;
+  c->mem_cap_bytes = int64_t(32) << 30;
+  c->tuner_cache = nullptr;
+}
+
+static std::string g_create_err;
+
+int ecc_create(const ecc_config* cfg, ecc_handle** out) {
+  if (!out) return ECC_ERR_ARG;
+  *out = nullptr;
+  ecc_handle* h = new (std::nothrow) ecc_handle();
+  if (!h) return ECC_ERR_OOM;
+  if (cfg)
+    h->cfg = *cfg;
+  else
+    ecc_config_default(&h->cfg);
+  if (h->cfg.convention != ECC_CONV_V && h->cfg.convention != ECC_CONV_T) {
+    g_create_err = "convention must be ECC_CONV_V or ECC_CONV_T";
+    delete h;
+    return ECC_ERR_ARG;
+  }
+  if (h->cfg.bins < 0 || h->cfg.bins > (int64_t(1) << 24) || h->cfg.slab_depth < 0 ||
+      h->cfg.ring_bytes < 0 || h->cfg.mem_cap_bytes < 0) {
+    g_create_err = "negative or oversized config field";
+    delete h;
+    return ECC_ERR_ARG;
+  }
+  if (h->cfg.slab_depth == 0) h->cfg.slab_depth = 64;
+  if (h->cfg.ring_bytes == 0) h->cfg.ring_bytes = int64_t(4) << 30;
+  if (h->cfg.mem_cap_bytes == 0) h->cfg.mem_cap_bytes = int64_t(32) << 30;
+  h->device = h->cfg.device;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || h->device < 0 || h->device >= ndev) {
+    g_create_err = std::string("no CUDA device ") + std::to_string(h->device) +
+                   (e != cudaSuccess ? std::string(": ") + cudaGetErrorString(e) : "");
+    cudaGetLastError();
+    delete h;
+    return ECC_ERR_CUDA;
+  }
+  if ((e = cudaSetDevice(h->device)) ||
+      (e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device)) ||
+      (e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) ||
+      (e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking)) ||
+      (e = h->errw.ensure(sizeof(int))) ||
+      (e = cudaMemset(h->errw.p, 0, sizeof(int))) ||
+      (e = cudaMallocHost(&h->h_err, sizeof(int)))) {
+    g_create_err = std::string("CUDA setup: ") + cudaGetErrorString(e);
+    ecc_destroy(h);
+    return e == cudaErrorMemoryAllocation ? ECC_ERR_OOM : ECC_ERR_CUDA;
+  }
+  *out = h;
+  return ECC_OK;
+}
+
+void ecc_destroy(ecc_handle* h) {
+  if (!h) return;
+  try {
+    serve_shutdown(h);
+  } catch (...) {
+  }
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
+  for (DevBuf* b : {&h->img, &h->vcec, &h->curve, &h->errw, &h->pairs, &h->pair_count, &h->tmp,
+                    &h->out_keys, &h->out_chi, &h->out_count, &h->batch_desc, &h->batch_items,
+                    &h->batch_vcec, &h->batch_curve})
+    b->release();
+  for (auto& pr : h->prof_events) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  if (h->h_err) cudaFreeHost(h->h_err);
+  if (h->stream) cudaStreamDestroy(h->stream);
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+  delete h;
+}
+
+const char* ecc_last_error(const ecc_handle* h) {
+  return h ? h->err.c_str() : g_create_err.c_str();
+}
+
+void ecc_result_free(ecc_result* r) {
+  if (!r) return;
+  if (r->owned) {
+    std::free(r->curve);
+    std::free(r->thresholds);
+    std::free(r->chi);
+  }
+  r->curve = nullptr;
+  r->thresholds = nullptr;
+  r->chi = nullptr;
+  r->owned = 0;
+  r->bins = 0;
+  r->npairs = 0;
+}
+
+int ecc_compute(ecc_handle* h, const void* image, const int64_t* dims, int ndim,
+                ecc_dtype dtype, ecc_result* out) {
+  if (!h) return ECC_ERR_ARG;
+  try {
+    std::lock_guard<std::mutex> lk(h->api_mu);
+    h->err.clear();
+    if (!out) return set_err(h, ECC_ERR_ARG, "out is NULL");
+    std::memset(out, 0, sizeof *out);
+    out->owned = 1;
+    Shape s;
+    int rc = validate_shape(h, dims, ndim, &s);
+    if (rc) return rc;
+    const size_t eb = dtype_bytes(dtype);
+    if (!eb) return set_err(h, ECC_ERR_DTYPE, "unknown dtype %d", (int)dtype);
+    if (s.voxels > 0 && !image) return set_err(h, ECC_ERR_ARG, "image is NULL");
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e) return cuda_err(h, e, "set device");
+    const void* d_img = image;
+    if (s.voxels > 0 && !is_device_ptr(h, image)) {
+      if ((e = h->img.ensure(eb * s.voxels))) return cuda_err(h, e, "image buffer");
+      if ((e = cudaMemcpyAsync(h->img.p, image, eb * s.voxels, cudaMemcpyHostToDevice,
+                               h->stream)))
+        return cuda_err(h, e, "copy image");
+      d_img = h->img.p;
+    }
+    if ((e = cudaMemsetAsync(h->errw.p, 0, sizeof(int), h->stream)))
+      return cuda_err(h, e, "memset");
+    if (dtype == ECC_F32) {
+      out->bins = 0;
+      if (s.voxels == 0) {
+        out->thresholds = static_cast<float*>(std::malloc(sizeof(float)));
+        out->chi = static_cast<int64_t*>(std::malloc(sizeof(int64_t)));
+        return ECC_OK;
+      }
+      rc = compute_float(h, d_img, s, out);
+      if (rc) ecc_result_free(out);
+      return rc;
+    }
+    const int64_t bins = default_bins(h, dtype);
+    if (dtype == ECC_U8 && bins > 256 && h->cfg.bins == 0) return set_err(h, ECC_ERR_ARG, "bins");
+    if ((e = h->vcec.ensure(sizeof(long long) * bins)) ||
+        (e = h->curve.ensure(sizeof(long long) * bins)))
+      return cuda_err(h, e, "vcec buffers");
+    rc = enqueue_int(h, d_img, s, dtype, bins, h->vcec.as<long long>(), h->curve.as<long long>(),
+                     h->stream);
+    if (rc) return rc;
+    out->bins = bins;
+    out->curve = static_cast<int64_t*>(std::malloc(sizeof(int64_t) * bins));
+    if (!out->curve) return set_err(h, ECC_ERR_OOM, "host curve");
+    if ((e = cudaMemcpyAsync(out->curve, h->curve.p, sizeof(int64_t) * bins,
+                             cudaMemcpyDeviceToHost, h->stream)))
+      return cuda_err(h, e, "copy curve");
+    int word = 0;
+    if ((rc = read_err_word(h, h->stream, &word))) return rc;
+    if ((rc = err_word_status(h, word))) {
+      ecc_result_free(out);
+      return rc;
+    }
+    return ECC_OK;
+  } catch (const std::bad_alloc&) {
+    return set_err(h, ECC_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return set_err(h, ECC_ERR_CUDA, "internal error");
+  }
+}
+
+int ecc_compute_device(ecc_handle* h, const void* d_image, const int64_t* dims, int ndim,
+                       ecc_dtype dtype, int64_t bins, int64_t* d_curve, void* stream) {
+  if (!h) return ECC_ERR_ARG;
+  try {
+    std::lock_guard<std::mutex> lk(h->api_mu);
+    h->err.clear();
+    Shape s;
+    int rc = validate_shape(h, dims, ndim, &s);
+    if (rc) return rc;
+    if (dtype != ECC_U8 && dtype != ECC_U16)
+      return set_err(h, ECC_ERR_DTYPE, "ecc_compute_device takes ECC_U8 or ECC_U16");
+    if (bins <= 0) bins = default_bins(h, dtype);
+    if (bins > (int64_t(1) << 24)) return set_err(h, ECC_ERR_ARG, "bins too large");
+    if (!d_curve || (s.voxels > 0 && !d_image))
+      return set_err(h, ECC_ERR_ARG, "null device pointer");
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e) return cuda_err(h, e, "set device");
+    if ((e = h->vcec.ensure(sizeof(long long) * bins))) return cuda_err(h, e, "vcec buffer");
+    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : h->stream;
+    return enqueue_int(h, d_image, s, dtype, bins, h->vcec.as<long long>(),
+                       reinterpret_cast<long long*>(d_curve), st);
+  } catch (...) {
+    return set_err(h, ECC_ERR_CUDA, "internal error");
+  }
+}
+
+int ecc_device_status(ecc_handle* h) {
+  if (!h) return ECC_ERR_ARG;
+  try {
+    std::lock_guard<std::mutex> lk(h->api_mu);
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e) return cuda_err(h, e, "set device");
+    if ((e = cudaDeviceSynchronize())) return cuda_err(h, e, "synchronize");
+    int word = 0;
+    int rc = read_err_word(h, h->stream, &word);
+    if (rc) return rc;
+    if ((e = cudaMemsetAsync(h->errw.p, 0, sizeof(int), h->stream)))
+      return cuda_err(h, e, "memset");
+    if ((rc = sync_stream(h, h->stream))) return rc;
+    return err_word_status(h, word);
+  } catch (...) {
+    return set_err(h, ECC_ERR_CUDA, "internal error");
+  }
+}
+
+int64_t ecc_launch_count(const ecc_handle* h) { return h ? h->launches.load() : 0; }
+
+int ecc_set_profiling(ecc_handle* h, int on) {
+  if (!h) return ECC_ERR_ARG;
+  std::lock_guard<std::mutex> lk(h->api_mu);
+  h->prof_on = on != 0;
+  return ECC_OK;
+}
+
+int ecc_profile_read(ecc_handle* h, double* contrib_ms, int64_t* count) {
+  if (!h || !contrib_ms || !count) return ECC_ERR_ARG;
+  std::lock_guard<std::mutex> lk(h->api_mu);
+  double total = 0.0;
+  int rc = ECC_OK;
+  for (auto& pr : h->prof_events) {
+    if (rc == ECC_OK) rc = wait_event(h, pr.second, 300LL * 1000 * 1000);
+    float ms = 0.f;
+    if (rc == ECC_OK) {
+      cudaError_t e = cudaEventElapsedTime(&ms, pr.first, pr.second);
+      if (e) rc = cuda_err(h, e, "elapsed time");
+    }
+    total += ms;
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  *count = (int64_t)h->prof_events.size();
+  h->prof_events.clear();
+  *contrib_ms = total;
+  return rc;
+}
+
+}  // extern "C"

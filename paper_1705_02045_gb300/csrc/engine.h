@@ -1,0 +1,107 @@
+// Host engine shared by the C-ABI translation units (not a public header).
+#pragma once
+
+#include <atomic>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/ecc.h"
+#include "ecc_internal.h"
+
+namespace ecc {
+
+// A growable device allocation owned by the handle.
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= cap && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    const size_t want = bytes < 256 ? 256 : bytes;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e == cudaSuccess) cap = want;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+  template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+// A shape validated and viewed as 3D/4D for the kernels.
+struct Shape {
+  int ndim = 0;
+  int64_t dims[4] = {0, 0, 0, 0};
+  int64_t voxels = 0;
+  int view = 3;
+  int64_t n[4] = {1, 1, 1, 1};
+};
+
+struct Request;  // serving (batch.cu)
+
+}  // namespace ecc
+
+struct ecc_handle {
+  ecc_config cfg{};
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;       // compute
+  cudaStream_t copy_stream = nullptr;  // host <-> device
+  std::string err;
+  std::mutex api_mu;                    // serialises the blocking entry points
+  std::atomic<int64_t> launches{0};
+  int64_t launch_tmp = 0;
+
+  ecc::DevBuf img, vcec, curve, errw, pairs, pair_count, tmp, out_keys, out_chi, out_count;
+  ecc::DevBuf batch_desc, batch_items, batch_vcec, batch_curve;
+  int* h_err = nullptr;                 // pinned scalar for error readback
+
+  // instrumentation: event pairs around contribution kernels
+  bool prof_on = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
+
+  // serving state (batch.cu)
+  std::mutex sv_mu;
+  std::condition_variable sv_cv;
+  std::thread sv_thread;
+  bool sv_stop = false;
+  bool sv_started = false;
+  uint64_t sv_next_id = 1;
+  std::deque<ecc::Request*> sv_queue;
+  std::map<uint64_t, ecc::Request*> sv_all;
+  int64_t sv_bytes_in_use = 0;
+  cudaStream_t sv_stream = nullptr;
+  cudaStream_t sv_copy_stream = nullptr;
+};
+
+namespace ecc {
+
+int set_err(ecc_handle* h, int code, const char* fmt, ...);
+int cuda_err(ecc_handle* h, cudaError_t e, const char* what);
+int validate_shape(ecc_handle* h, const int64_t* dims, int ndim, Shape* s);
+int64_t default_bins(const ecc_handle* h, int dtype);
+size_t dtype_bytes(int dtype);
+bool is_device_ptr(const ecc_handle* h, const void* p);
+// Enqueues VCEC accumulation (zeroed first) + contribution kernel + scan of
+// an integer image already on the device.
+int enqueue_int(ecc_handle* h, const void* d_img, const Shape& s, int dtype, int64_t bins,
+                long long* d_vcec, long long* d_curve, cudaStream_t stream);
+// Bounded wait on an event (host side); ECC_ERR_TIMEOUT after timeout_us.
+int wait_event(ecc_handle* h, cudaEvent_t ev, int64_t timeout_us);
+cudaError_t launch_local(const LocalArgs& a, int num_sms, int64_t* launches);
+void serve_shutdown(ecc_handle* h);
+
+}  // namespace ecc

@@ -1,0 +1,299 @@
+"""Python binding of libecc_gb300.so (include/ecc.h), argument marshalling only.
+
+Every function keeps the C name. Images may be numpy arrays (host) or torch
+tensors (host or CUDA); the library itself tells host from device pointers.
+There is no Python or CPU fallback: if the library is missing, ``load()``
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ECC_OK, ECC_PENDING = 0, 1
+ECC_ERR_ARG, ECC_ERR_DTYPE, ECC_ERR_VALUE, ECC_ERR_OOM = -1, -2, -3, -4
+ECC_ERR_TIMEOUT, ECC_ERR_STATE, ECC_ERR_CUDA = -5, -6, -7
+ECC_U8, ECC_U16, ECC_F32 = 1, 2, 3
+ECC_CONV_V, ECC_CONV_T = 0, 1
+
+_STATUS = {0: "ECC_OK", 1: "ECC_PENDING", -1: "ECC_ERR_ARG", -2: "ECC_ERR_DTYPE",
+           -3: "ECC_ERR_VALUE", -4: "ECC_ERR_OOM", -5: "ECC_ERR_TIMEOUT",
+           -6: "ECC_ERR_STATE", -7: "ECC_ERR_CUDA"}
+
+
+class EccError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class ecc_config(C.Structure):
+    _fields_ = [("device", C.c_int), ("convention", C.c_int), ("bins", C.c_int64),
+                ("slab_depth", C.c_int64), ("ring_bytes", C.c_int64),
+                ("mem_cap_bytes", C.c_int64), ("tuner_cache", C.c_char_p)]
+
+
+class ecc_result(C.Structure):
+    _fields_ = [("bins", C.c_int64), ("curve", C.POINTER(C.c_int64)),
+                ("npairs", C.c_int64), ("thresholds", C.POINTER(C.c_float)),
+                ("chi", C.POINTER(C.c_int64)), ("owned", C.c_int32), ("status", C.c_int32)]
+
+
+class ecc_image(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("dims", C.c_int64 * 4), ("ndim", C.c_int32),
+                ("dtype", C.c_int32), ("bins", C.c_int64)]
+
+
+_P = C.c_void_p
+_I64P = C.POINTER(C.c_int64)
+_SIGNATURES = {
+    "ecc_config_default": (None, [C.POINTER(ecc_config)]),
+    "ecc_create": (C.c_int, [C.POINTER(ecc_config), C.POINTER(_P)]),
+    "ecc_destroy": (None, [_P]),
+    "ecc_last_error": (C.c_char_p, [_P]),
+    "ecc_result_free": (None, [C.POINTER(ecc_result)]),
+    "ecc_compute": (C.c_int, [_P, _P, _I64P, C.c_int, C.c_int, C.POINTER(ecc_result)]),
+    "ecc_compute_device": (C.c_int, [_P, _P, _I64P, C.c_int, C.c_int, C.c_int64, _P, _P]),
+    "ecc_device_status": (C.c_int, [_P]),
+    "ecc_stream_begin": (C.c_int, [_P, _I64P, C.c_int, C.c_int, C.POINTER(_P)]),
+    "ecc_stream_push_slab": (C.c_int, [_P, _P, C.c_int64, C.c_int64]),
+    "ecc_stream_finish": (C.c_int, [_P, C.POINTER(ecc_result)]),
+    "ecc_stream_abort": (None, [_P]),
+    "ecc_compute_batch": (C.c_int, [_P, C.c_int, C.POINTER(ecc_image), C.POINTER(ecc_result)]),
+    "ecc_submit": (C.c_int, [_P, _P, _I64P, C.c_int, C.c_int, C.POINTER(C.c_uint64)]),
+    "ecc_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(ecc_result), C.c_int64]),
+    "ecc_request_latency_us": (C.c_int, [_P, C.c_uint64, C.POINTER(C.c_double)]),
+    "ecc_launch_count": (C.c_int64, [_P]),
+    "ecc_set_profiling": (C.c_int, [_P, C.c_int]),
+    "ecc_profile_read": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Loads the CUDA library (raises if it is not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build_library()
+        else:
+            raise RuntimeError(
+                f"{path} is missing: build it with __graft_entry__.build() "
+                "(there is no CPU fallback)")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _dtype_code(dt) -> int:
+    name = str(dt).replace("torch.", "")
+    return {"uint8": ECC_U8, "uint16": ECC_U16, "float32": ECC_F32}[name]
+
+
+def _check(h, rc: int) -> int:
+    if rc < 0:
+        msg = load().ecc_last_error(h)
+        raise EccError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _dims(shape):
+    return (C.c_int64 * max(1, len(shape)))(*[int(s) for s in shape])
+
+
+def _data_ptr(image):
+    """(pointer, keepalive) of a numpy array or torch tensor (C order)."""
+    if isinstance(image, np.ndarray):
+        arr = np.ascontiguousarray(image)
+        return arr.ctypes.data_as(C.c_void_p), arr
+    if not image.is_contiguous():
+        image = image.contiguous()
+    return C.c_void_p(image.data_ptr()), image
+
+
+def _result_to_numpy(r: ecc_result):
+    if r.bins > 0:
+        return np.ctypeslib.as_array(r.curve, shape=(r.bins,)).copy()
+    if r.npairs > 0:
+        t = np.ctypeslib.as_array(r.thresholds, shape=(r.npairs,)).copy()
+        chi = np.ctypeslib.as_array(r.chi, shape=(r.npairs,)).copy()
+        return t, chi
+    return np.zeros(0, np.float32), np.zeros(0, np.int64)
+
+
+def ecc_config_default() -> ecc_config:
+    cfg = ecc_config()
+    load().ecc_config_default(C.byref(cfg))
+    return cfg
+
+
+def ecc_create(config: ecc_config | None = None, **fields):
+    lib = load()
+    cfg = config if config is not None else ecc_config_default()
+    for k, v in fields.items():
+        setattr(cfg, k, v)
+    h = C.c_void_p()
+    rc = lib.ecc_create(C.byref(cfg), C.byref(h))
+    if rc != ECC_OK:
+        msg = lib.ecc_last_error(None)
+        raise EccError(rc, msg.decode() if msg else "")
+    return h
+
+
+def ecc_destroy(h) -> None:
+    load().ecc_destroy(h)
+
+
+def ecc_last_error(h) -> str:
+    msg = load().ecc_last_error(h)
+    return msg.decode() if msg else ""
+
+
+def ecc_compute(h, image):
+    """Curve of an integer image (int64[bins]) or (thresholds, chi) of a float
+    image; `image` is a numpy array or a torch tensor (host or CUDA)."""
+    lib = load()
+    ptr, keep = _data_ptr(image)
+    dims = _dims(image.shape)
+    r = ecc_result()
+    _check(h, lib.ecc_compute(h, ptr, dims, len(image.shape), _dtype_code(image.dtype),
+                              C.byref(r)))
+    try:
+        return _result_to_numpy(r)
+    finally:
+        lib.ecc_result_free(C.byref(r))
+        del keep
+
+
+def ecc_compute_device(h, d_image, bins: int, d_curve, stream=None) -> None:
+    """Enqueues an integer CUDA-tensor image; writes the int64 CUDA tensor
+    ``d_curve[bins]``; ``stream`` is a torch.cuda.Stream or None."""
+    lib = load()
+    dims = _dims(d_image.shape)
+    st = C.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(h, lib.ecc_compute_device(h, C.c_void_p(d_image.data_ptr()), dims,
+                                     len(d_image.shape), _dtype_code(d_image.dtype),
+                                     int(bins), C.c_void_p(d_curve.data_ptr()), st))
+
+
+def ecc_device_status(h) -> int:
+    return _check(h, load().ecc_device_status(h))
+
+
+def ecc_stream_begin(h, shape, dtype):
+    s = C.c_void_p()
+    _check(h, load().ecc_stream_begin(h, _dims(shape), len(shape), _dtype_code(dtype),
+                                      C.byref(s)))
+    return s
+
+
+def ecc_stream_push_slab(h, s, planes, z0: int) -> None:
+    ptr, keep = _data_ptr(planes)
+    _check(h, load().ecc_stream_push_slab(s, ptr, int(z0), int(planes.shape[0])))
+    del keep
+
+
+def ecc_stream_finish(h, s):
+    lib = load()
+    r = ecc_result()
+    _check(h, lib.ecc_stream_finish(s, C.byref(r)))
+    try:
+        return _result_to_numpy(r)
+    finally:
+        lib.ecc_result_free(C.byref(r))
+
+
+def ecc_stream_abort(s) -> None:
+    load().ecc_stream_abort(s)
+
+
+def ecc_compute_batch(h, images, bins=None):
+    """Curves of a list of integer images (numpy or torch, host or CUDA) from
+    one batched launch. Returns a list of int64 arrays (or EccError objects
+    for images that failed)."""
+    lib = load()
+    n = len(images)
+    descs = (ecc_image * max(n, 1))()
+    keep = []
+    for i, im in enumerate(images):
+        ptr, k = _data_ptr(im)
+        keep.append(k)
+        descs[i].data = ptr.value
+        for j, s in enumerate(im.shape):
+            descs[i].dims[j] = int(s)
+        descs[i].ndim = len(im.shape)
+        descs[i].dtype = _dtype_code(im.dtype)
+        descs[i].bins = int(bins[i]) if bins is not None else 0
+    outs = (ecc_result * max(n, 1))()
+    _check(h, lib.ecc_compute_batch(h, n, descs, outs))
+    res = []
+    for i in range(n):
+        if outs[i].status != ECC_OK:
+            res.append(EccError(outs[i].status, f"image {i}"))
+        else:
+            res.append(_result_to_numpy(outs[i]))
+        lib.ecc_result_free(C.byref(outs[i]))
+    return res
+
+
+def ecc_submit(h, image) -> int:
+    lib = load()
+    ptr, keep = _data_ptr(image)
+    rid = C.c_uint64()
+    _check(h, lib.ecc_submit(h, ptr, _dims(image.shape), len(image.shape),
+                             _dtype_code(image.dtype), C.byref(rid)))
+    del keep
+    return rid.value
+
+
+def ecc_poll(h, req_id: int, timeout_us: int = 0):
+    """(status, curve or None)."""
+    lib = load()
+    r = ecc_result()
+    rc = lib.ecc_poll(h, C.c_uint64(req_id), C.byref(r), int(timeout_us))
+    if rc == ECC_OK:
+        try:
+            return rc, _result_to_numpy(r)
+        finally:
+            lib.ecc_result_free(C.byref(r))
+    if rc in (ECC_PENDING, ECC_ERR_TIMEOUT):
+        return rc, None
+    _check(h, rc)
+    return rc, None
+
+
+def ecc_request_latency_us(h, req_id: int) -> float:
+    v = C.c_double()
+    _check(h, load().ecc_request_latency_us(h, C.c_uint64(req_id), C.byref(v)))
+    return v.value
+
+
+def ecc_launch_count(h) -> int:
+    return int(load().ecc_launch_count(h))
+
+
+def ecc_set_profiling(h, on: bool) -> None:
+    _check(h, load().ecc_set_profiling(h, 1 if on else 0))
+
+
+def ecc_profile_read(h):
+    """(summed contribution-kernel milliseconds, number of computations)."""
+    ms, n = C.c_double(), C.c_int64()
+    _check(h, load().ecc_profile_read(h, C.byref(ms), C.byref(n)))
+    return ms.value, n.value

@@ -1,0 +1,248 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, element by
+element (integers: bit-exact; float pairs: exact keys and exact int64 chi).
+
+Cases span several tiles with ragged tails in every axis, the degenerate
+shapes (single voxel, a single row or column, empty), prime extents, both cell
+conventions, every dtype and both histogram paths (shared memory for up to
+16384 bins, global memory above).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1705_02045_gb300 import ecc, synth
+
+pytestmark = pytest.mark.gpu
+
+S = synth.SEED_BASE
+
+
+@pytest.fixture(scope="module")
+def hV(lib):
+    h = ecc.ecc_create(device=0, convention=ecc.ECC_CONV_V)
+    yield h
+    ecc.ecc_destroy(h)
+
+
+@pytest.fixture(scope="module")
+def hT(lib):
+    h = ecc.ecc_create(device=0, convention=ecc.ECC_CONV_T)
+    yield h
+    ecc.ecc_destroy(h)
+
+
+def _handle(hV, hT, conv):
+    return hV if conv == "V" else hT
+
+
+INT_SHAPES = [(1,), (7,), (1000,), (100003,), (1, 1), (1, 50), (50, 1), (33, 65),
+              (1, 1, 1), (2, 3, 4), (17, 9, 33), (31, 37, 41), (5, 70, 3),
+              (2, 2, 2, 2), (3, 5, 7, 9), (7, 6, 35, 5), (4, 9, 3, 66)]
+
+
+@pytest.mark.parametrize("conv", ["V", "T"])
+@pytest.mark.parametrize("shape", INT_SHAPES, ids=str)
+def test_u8_uniform(hV, hT, conv, shape):
+    img = synth.uniform_u8(shape, S + 10 + len(shape))
+    got = ecc.ecc_compute(_handle(hV, hT, conv), img)
+    assert np.array_equal(got, oracle.ecc_int(img, 256, conv))
+
+
+@pytest.mark.parametrize("conv", ["V", "T"])
+@pytest.mark.parametrize("shape", [(40, 45), (19, 40, 37), (6, 11, 10, 13)], ids=str)
+def test_u8_smooth_with_ties(hV, hT, conv, shape):
+    """Smooth, requantised fields have plateaus: the index tie-break matters."""
+    img = synth.smooth_u8(shape, 1.5, S + 20)
+    got = ecc.ecc_compute(_handle(hV, hT, conv), img)
+    assert np.array_equal(got, oracle.ecc_int(img, 256, conv))
+
+
+@pytest.mark.parametrize("shape", [(3, 5), (9, 8, 7), (4, 5, 6, 3)], ids=str)
+def test_few_levels_many_ties(hV, shape):
+    img = synth.uniform_int(shape, 3, S + 30, np.uint8)
+    assert np.array_equal(ecc.ecc_compute(hV, img), oracle.ecc_int(img, 256, "V"))
+
+
+def test_small_bins(lib):
+    h = ecc.ecc_create(device=0, bins=8)
+    try:
+        img = synth.uniform_int((13, 14, 15), 8, S + 31, np.uint8)
+        got = ecc.ecc_compute(h, img)
+        assert got.shape == (8,)
+        assert np.array_equal(got, oracle.ecc_int(img, 8, "V"))
+    finally:
+        ecc.ecc_destroy(h)
+
+
+@pytest.mark.parametrize("shape", [(21, 33, 40), (5, 6, 7, 8)], ids=str)
+def test_u16_14bit_smem_histogram(lib, shape):
+    h = ecc.ecc_create(device=0, bins=16384)
+    try:
+        img = synth.two_phase_u16(shape, 2.0, S + 40)
+        assert np.array_equal(ecc.ecc_compute(h, img), oracle.ecc_int(img, 16384, "V"))
+    finally:
+        ecc.ecc_destroy(h)
+
+
+@pytest.mark.parametrize("conv", ["V", "T"])
+def test_u16_full_range_global_histogram(hV, hT, conv):
+    img = synth.uniform_int((9, 40, 35), 65536, S + 41, np.uint16)
+    got = ecc.ecc_compute(_handle(hV, hT, conv), img)
+    assert got.shape == (65536,)
+    assert np.array_equal(got, oracle.ecc_int(img, 65536, conv))
+
+
+@pytest.mark.parametrize("conv", ["V", "T"])
+@pytest.mark.parametrize("shape", [(1,), (9,), (9, 13), (8, 9, 10), (6, 7, 8, 9), (3, 40, 2, 35)],
+                         ids=str)
+def test_f32_pairs(hV, hT, conv, shape):
+    img = synth.grf_f32(shape, 1.2, S + 50)
+    t, chi = ecc.ecc_compute(_handle(hV, hT, conv), img)
+    t_ref, chi_ref = oracle.ecc_pairs_float(img, conv)
+    assert np.array_equal(t, t_ref)
+    assert np.array_equal(chi, chi_ref)
+
+
+def test_f32_ties_and_signed_zero(hV):
+    rng = np.random.default_rng(S + 51)
+    img = (rng.integers(-3, 4, size=(10, 11, 12)) * 0.5).astype(np.float32)
+    img[img == 0] = np.where(rng.random(np.sum(img == 0)) < 0.5, -0.0, 0.0)
+    t, chi = ecc.ecc_compute(hV, img)
+    t_ref, chi_ref = oracle.ecc_pairs_float(img, "V")
+    assert np.array_equal(t, t_ref) and np.array_equal(chi, chi_ref)
+    assert not np.any(np.signbit(t[t == 0]))
+
+
+def test_golden_fixtures(hV, hT, lib):
+    path = os.path.join(os.path.dirname(__file__), "golden", "oracle_small.json")
+    for rec in json.load(open(path)):
+        img = np.array(rec["values"], dtype=rec["dtype"]).reshape(rec["shape"])
+        for conv in ("V", "T"):
+            h = _handle(hV, hT, conv)
+            if rec["dtype"] == "float32":
+                t, chi = ecc.ecc_compute(h, img)
+                assert [[float(a), int(b)] for a, b in zip(t, chi)] == rec["pairs_" + conv]
+            else:
+                hb = ecc.ecc_create(device=0, bins=rec["bins"],
+                                    convention=0 if conv == "V" else 1)
+                try:
+                    curve = ecc.ecc_compute(hb, img)
+                finally:
+                    ecc.ecc_destroy(hb)
+                a = np.diff(np.r_[0, curve])
+                nz = np.flatnonzero(a)
+                assert [[int(x), int(a[x])] for x in nz] == rec["vcec_" + conv], rec["name"]
+
+
+# ---- edge cases and errors -------------------------------------------------
+
+def test_empty_image(hV):
+    got = ecc.ecc_compute(hV, np.zeros((0, 5, 5), np.uint8))
+    assert got.shape == (256,) and not got.any()
+    t, chi = ecc.ecc_compute(hV, np.zeros((4, 0), np.float32))
+    assert t.size == 0 and chi.size == 0
+
+
+def test_value_out_of_range(lib):
+    h = ecc.ecc_create(device=0, bins=16)
+    try:
+        img = np.zeros((4, 5, 6), np.uint8)
+        img[2, 3, 4] = 16
+        with pytest.raises(ecc.EccError) as ei:
+            ecc.ecc_compute(h, img)
+        assert ei.value.status == ecc.ECC_ERR_VALUE
+        # the handle stays usable
+        img[2, 3, 4] = 15
+        assert np.array_equal(ecc.ecc_compute(h, img), oracle.ecc_int(img, 16, "V"))
+    finally:
+        ecc.ecc_destroy(h)
+
+
+@pytest.mark.parametrize("bad", [np.nan, np.inf, -np.inf])
+def test_nan_inf_rejected(hV, bad):
+    img = np.zeros((3, 4, 5), np.float32)
+    img[1, 2, 3] = bad
+    with pytest.raises(ecc.EccError) as ei:
+        ecc.ecc_compute(hV, img)
+    assert ei.value.status == ecc.ECC_ERR_VALUE
+
+
+def test_bad_arguments(hV):
+    lib = ecc.load()
+    import ctypes as C
+    r = ecc.ecc_result()
+    dims = (C.c_int64 * 5)(2, 2, 2, 2, 2)
+    buf = np.zeros(32, np.uint8)
+    p = buf.ctypes.data_as(C.c_void_p)
+    assert lib.ecc_compute(hV, p, dims, 5, ecc.ECC_U8, C.byref(r)) == ecc.ECC_ERR_ARG
+    assert lib.ecc_compute(hV, p, dims, 0, ecc.ECC_U8, C.byref(r)) == ecc.ECC_ERR_ARG
+    neg = (C.c_int64 * 2)(2, -1)
+    assert lib.ecc_compute(hV, p, neg, 2, ecc.ECC_U8, C.byref(r)) == ecc.ECC_ERR_ARG
+    assert lib.ecc_compute(hV, p, dims, 2, 9, C.byref(r)) == ecc.ECC_ERR_DTYPE
+    assert lib.ecc_compute(hV, None, dims, 2, ecc.ECC_U8, C.byref(r)) == ecc.ECC_ERR_ARG
+    assert "NULL" in ecc.ecc_last_error(hV)
+
+
+# ---- device pointers --------------------------------------------------------
+
+def test_device_tensor_input(hV):
+    import torch
+    img = synth.smooth_u8((33, 40, 50), 2.0, S + 60)
+    t = torch.from_numpy(img).cuda()
+    assert np.array_equal(ecc.ecc_compute(hV, t), oracle.ecc_int(img, 256, "V"))
+
+
+def test_compute_device_on_torch_stream(hV):
+    import torch
+    img = synth.uniform_int((20, 30, 40), 16384, S + 61, np.uint16)
+    d = torch.from_numpy(img).cuda()
+    curve = torch.empty(16384, dtype=torch.int64, device="cuda")
+    s = torch.cuda.Stream()
+    ecc.ecc_compute_device(hV, d, 16384, curve, stream=s)
+    s.synchronize()
+    assert ecc.ecc_device_status(hV) == ecc.ECC_OK
+    assert np.array_equal(curve.cpu().numpy(), oracle.ecc_int(img, 16384, "V"))
+
+
+def test_device_status_reports_bad_value(lib):
+    import torch
+    h = ecc.ecc_create(device=0)
+    try:
+        img = torch.zeros((4, 4, 4), dtype=torch.uint8, device="cuda")
+        img[1, 1, 1] = 200
+        curve = torch.empty(100, dtype=torch.int64, device="cuda")
+        ecc.ecc_compute_device(h, img, 100, curve)
+        with pytest.raises(ecc.EccError) as ei:
+            ecc.ecc_device_status(h)
+        assert ei.value.status == ecc.ECC_ERR_VALUE
+        assert ecc.ecc_device_status(h) == ecc.ECC_OK  # flag cleared
+    finally:
+        ecc.ecc_destroy(h)
+
+
+# ---- the benchmark workloads at full size ----------------------------------
+
+def test_full_size_2d_512_uniform(hV):
+    img = synth.uniform_u8((512, 512), S + 0)
+    assert np.array_equal(ecc.ecc_compute(hV, img), oracle.ecc_int(img, 256, "V"))
+
+
+def test_full_size_3d_512_smooth_device_path(hV):
+    """The 512^3 smoothed uint8 workload in the launch configuration the
+    benchmark times (device-resident image, ecc_compute_device)."""
+    import torch
+    img = synth.smooth_u8((512, 512, 512), 4.0, S + 1)
+    d = torch.from_numpy(img).cuda()
+    curve = torch.empty(256, dtype=torch.int64, device="cuda")
+    ecc.ecc_compute_device(hV, d, 256, curve)
+    torch.cuda.synchronize()
+    assert ecc.ecc_device_status(hV) == ecc.ECC_OK
+    got = curve.cpu().numpy()
+    want = np.zeros(256, np.int64)
+    # oracle in z-ranges of cells (chunk decomposition; bounded host memory)
+    for lo in range(0, 513, 128):
+        want += oracle.vcec_int_zrange(img, 256, lo, min(lo + 128, 513), "V")
+    assert np.array_equal(got, oracle.ecc_from_vcec(want))

@@ -1,24 +1,791 @@
-// Batched and served computation (filled in by the persistent batched kernel).
+// Batched and served computation.
+//
+// The paper processes independent chunks with a pool of worker threads, each
+// keeping its own VCEC (Sec. 3, "Parallel Computations"). On the GPU the same
+// independence lets many images share one persistent launch: a work list of
+// (image, tile range) items, balanced by voxel work on the host, is walked by
+// a fixed grid; each block keeps a private shared-memory histogram per image
+// (flushed when the image changes) and every image has its own int64 VCEC.
+// The launch sequence (zero VCECs, batched contribution kernel, batched scan)
+// is captured once per slot in a CUDA graph whose kernels read the batch from
+// a fixed device descriptor buffer; a new batch only re-uploads the
+// descriptors and replays the graph.
+//
+// Serving (ecc_submit / ecc_poll): a scheduler thread admits requests while
+// their device memory fits under the cap, launches the admitted ones as a
+// batch on one of two slots (two streams), and keeps launching new batches
+// while earlier ones run (continuous batching). Completion is detected by
+// events; results move to the request, device memory returns to the cap.
+#include "ecc_scan.cuh"
+#include "ecc_tile.cuh"
 #include "engine.h"
 
+#include <chrono>
+#include <cstring>
+#include <new>
+
 namespace ecc {
-struct Request {};
-void serve_shutdown(ecc_handle*) {}
+
+struct BImage {
+  const void* img;
+  long long* vcec;
+  long long* curve;
+  int* err;
+  int64_t n[3];  // z, y, x
+  int64_t bins;
+  int64_t tiles_x, tiles_y, zc;
+  int dtype;
+  int smem_hist;
+};
+
+struct BItem {
+  int image;
+  int pad;
+  int64_t tile_lo, tile_hi;
+};
+
+struct BHeader {
+  int n_images;
+  int n_items;
+};
+
+constexpr int kMaxBatch = 1024;
+constexpr int64_t kSmallBins = 256;
+
+namespace {
+
+struct DescLayout {
+  size_t hdr = 0, imgs = 0, items = 0, starts = 0, total = 0;
+  int item_cap = 0;
+};
+
+DescLayout desc_layout(int grid) {
+  auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+  DescLayout L;
+  L.item_cap = kMaxBatch + grid + 1;
+  size_t o = 0;
+  L.hdr = o; o += up(sizeof(BHeader));
+  L.imgs = o; o += up(sizeof(BImage) * kMaxBatch);
+  L.items = o; o += up(sizeof(BItem) * L.item_cap);
+  L.starts = o; o += up(sizeof(int) * (grid + 1));
+  L.total = o;
+  return L;
+}
+
+template <int CONV, int SMEM_BINS>
+__global__ void __launch_bounds__(kTileThreads)
+k_batch3(const unsigned char* __restrict__ desc, DescLayout L) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* ring = reinterpret_cast<uint32_t*>(smem);
+  int8_t* g2 = reinterpret_cast<int8_t*>(ring + 4 * kT3PL);
+  int* hist = reinterpret_cast<int*>(g2 + 256);
+  const BImage* imgs = reinterpret_cast<const BImage*>(desc + L.imgs);
+  const BItem* items = reinterpret_cast<const BItem*>(desc + L.items);
+  const int* starts = reinterpret_cast<const int*>(desc + L.starts);
+  g2[threadIdx.x] = (int8_t)g2_entry(threadIdx.x);
+  for (int b = threadIdx.x; b < SMEM_BINS; b += kTileThreads) hist[b] = 0;
+  __syncthreads();
+  const int i0 = starts[blockIdx.x], i1 = starts[blockIdx.x + 1];
+  for (int it = i0; it < i1; ++it) {
+    const BItem item = items[it];
+    const BImage& im = imgs[item.image];
+    Sink s;
+    s.bins = im.bins;
+    s.vcec = im.vcec;
+    s.hist = hist;
+    s.err = im.err;
+    const bool smem_hist = im.smem_hist && im.bins <= SMEM_BINS;
+    const int64_t txy = im.tiles_x * im.tiles_y;
+    for (int64_t t = item.tile_lo; t < item.tile_hi; ++t) {
+      const int64_t tz = t / txy, rem = t - tz * txy;
+      const int64_t y0 = (rem / im.tiles_x) * kT3Y, x0 = (rem % im.tiles_x) * kT3X;
+      const int64_t z0 = tz * im.zc, z1 = min(z0 + im.zc, im.n[0]);
+      if (im.dtype == kU8) {
+        const uint8_t* p = static_cast<const uint8_t*>(im.img);
+        if (smem_hist)
+          run_tile3<uint8_t, CONV, kSmemHist>(p, im.n[0], im.n[1], im.n[2], 0, im.n[0], x0, y0,
+                                              z0, z1, ring, g2, s);
+        else
+          run_tile3<uint8_t, CONV, kGlobalHist>(p, im.n[0], im.n[1], im.n[2], 0, im.n[0], x0,
+                                                y0, z0, z1, ring, g2, s);
+      } else {
+        const uint16_t* p = static_cast<const uint16_t*>(im.img);
+        if (smem_hist)
+          run_tile3<uint16_t, CONV, kSmemHist>(p, im.n[0], im.n[1], im.n[2], 0, im.n[0], x0, y0,
+                                               z0, z1, ring, g2, s);
+        else
+          run_tile3<uint16_t, CONV, kGlobalHist>(p, im.n[0], im.n[1], im.n[2], 0, im.n[0], x0,
+                                                 y0, z0, z1, ring, g2, s);
+      }
+    }
+    if (smem_hist) flush_smem_hist(s);
+  }
+}
+
+__global__ void k_batch_zero(const unsigned char* __restrict__ desc, DescLayout L) {
+  const BHeader* hdr = reinterpret_cast<const BHeader*>(desc + L.hdr);
+  if ((int)blockIdx.x >= hdr->n_images) return;
+  const BImage& im = reinterpret_cast<const BImage*>(desc + L.imgs)[blockIdx.x];
+  for (int64_t b = threadIdx.x; b < im.bins; b += blockDim.x) im.vcec[b] = 0;
+  if (threadIdx.x == 0) *im.err = 0;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_batch_scan(const unsigned char* __restrict__ desc, DescLayout L) {
+  const BHeader* hdr = reinterpret_cast<const BHeader*>(desc + L.hdr);
+  if ((int)blockIdx.x >= hdr->n_images) return;
+  const BImage& im = reinterpret_cast<const BImage*>(desc + L.imgs)[blockIdx.x];
+  block_scan_curve(im.vcec, im.curve, im.bins);
+}
+
+template <int CONV, int SMEM_BINS>
+size_t batch_smem() {
+  return 4 * kT3PL * 4 + 256 + sizeof(int) * SMEM_BINS;
+}
+
+}  // namespace
+
+// One launch slot: stream, descriptor buffers, per-image arena and the two
+// captured graphs (small histograms <= 256 bins, large <= 16384 bins).
+struct Slot {
+  cudaStream_t stream = nullptr;
+  int grid_small = 0, grid_large = 0, grid = 0;
+  DescLayout L;
+  DevBuf desc;
+  unsigned char* h_desc = nullptr;
+  DevBuf arena;
+  unsigned char* h_arena = nullptr;
+  size_t h_arena_cap = 0;
+  cudaGraphExec_t exec_small = nullptr, exec_large = nullptr;
+  cudaEvent_t done = nullptr;
+};
+
+struct BatchEngine {
+  std::vector<Slot> slots;
+};
+
+namespace {
+
+struct ImgSpec {
+  const void* d_img;
+  int64_t n[3];
+  int dtype;
+  int64_t bins;
+};
+
+template <int CONV>
+cudaError_t capture_graph(Slot& sl, bool large, cudaGraphExec_t* out) {
+  cudaError_t e;
+  cudaGraph_t g = nullptr;
+  if ((e = cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal))) return e;
+  k_batch_zero<<<kMaxBatch, 256, 0, sl.stream>>>(sl.desc.as<unsigned char>(), sl.L);
+  if (large)
+    k_batch3<CONV, kSmemBinsMax><<<sl.grid, kTileThreads, batch_smem<CONV, kSmemBinsMax>(),
+                                   sl.stream>>>(sl.desc.as<unsigned char>(), sl.L);
+  else
+    k_batch3<CONV, kSmallBins><<<sl.grid, kTileThreads, batch_smem<CONV, kSmallBins>(),
+                                 sl.stream>>>(sl.desc.as<unsigned char>(), sl.L);
+  k_batch_scan<<<kMaxBatch, kScanThreads, 0, sl.stream>>>(sl.desc.as<unsigned char>(), sl.L);
+  e = cudaStreamEndCapture(sl.stream, &g);
+  if (e) return e;
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  return e;
+}
+
+template <int CONV>
+cudaError_t grid_for(int num_sms, int* g_small, int* g_large) {
+  cudaError_t e;
+  auto ks = k_batch3<CONV, kSmallBins>;
+  auto kl = k_batch3<CONV, kSmemBinsMax>;
+  const size_t ss = batch_smem<CONV, kSmallBins>(), sl = batch_smem<CONV, kSmemBinsMax>();
+  if ((e = cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss)) ||
+      (e = cudaFuncSetAttribute(kl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl)))
+    return e;
+  int ps = 0, pl = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, ks, kTileThreads, ss)) ||
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pl, kl, kTileThreads, sl)))
+    return e;
+  *g_small = std::max(ps, 1) * num_sms;
+  *g_large = std::max(pl, 1) * num_sms;
+  return cudaSuccess;
+}
+
+int slot_init(ecc_handle* h, Slot& sl) {
+  cudaError_t e;
+  int gs = 0, gl = 0;
+  e = h->cfg.convention == kConvT ? grid_for<kConvT>(h->num_sms, &gs, &gl)
+                                  : grid_for<kConvV>(h->num_sms, &gs, &gl);
+  if (e) return cuda_err(h, e, "batch occupancy");
+  sl.grid_small = gs;
+  sl.grid_large = gl;
+  sl.grid = std::max(gs, gl);  // one descriptor layout fits both graphs
+  sl.L = desc_layout(sl.grid);
+  if ((e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking)) ||
+      (e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming)) ||
+      (e = sl.desc.ensure(sl.L.total)) ||
+      (e = cudaMallocHost(&sl.h_desc, sl.L.total)))
+    return cuda_err(h, e, "batch slot");
+  std::memset(sl.h_desc, 0, sl.L.total);
+  return ECC_OK;
+}
+
+void slot_free(Slot& sl) {
+  if (sl.stream) cudaStreamSynchronize(sl.stream);
+  if (sl.exec_small) cudaGraphExecDestroy(sl.exec_small);
+  if (sl.exec_large) cudaGraphExecDestroy(sl.exec_large);
+  if (sl.h_desc) cudaFreeHost(sl.h_desc);
+  if (sl.h_arena) cudaFreeHost(sl.h_arena);
+  sl.desc.release();
+  sl.arena.release();
+  if (sl.done) cudaEventDestroy(sl.done);
+  if (sl.stream) cudaStreamDestroy(sl.stream);
+  sl = Slot();
+}
+
+// Per-image arena record: vcec[bins], curve[bins], err word.
+size_t arena_bytes(int64_t bins) { return sizeof(long long) * (2 * bins + 1); }
+
+// Fills the slot's host descriptors for `specs` and uploads them; launches the
+// captured graph; copies curves and error words to the slot's pinned arena.
+// Returns the ECC status; on success *large tells which graph ran.
+int slot_run(ecc_handle* h, Slot& sl, const std::vector<ImgSpec>& specs, cudaStream_t wait_on,
+             cudaEvent_t wait_ev) {
+  cudaError_t e;
+  const int n = (int)specs.size();
+  bool large = false;
+  size_t arena_total = 0;
+  for (const ImgSpec& sp : specs) {
+    if (sp.bins > kSmallBins && sp.bins <= kSmemBinsMax) large = true;
+    arena_total += arena_bytes(sp.bins);
+  }
+  if ((e = sl.arena.ensure(arena_total))) return cuda_err(h, e, "batch arena");
+  if (sl.h_arena_cap < arena_total) {
+    if (sl.h_arena) cudaFreeHost(sl.h_arena);
+    sl.h_arena = nullptr;
+    if ((e = cudaMallocHost(&sl.h_arena, arena_total))) {
+      sl.h_arena_cap = 0;
+      return cuda_err(h, e, "pinned arena");
+    }
+    sl.h_arena_cap = arena_total;
+  }
+  const int grid = large ? sl.grid_large : sl.grid_small;
+  // work list: tiles of every image, cut into per-block items of equal work
+  BHeader* hdr = reinterpret_cast<BHeader*>(sl.h_desc + sl.L.hdr);
+  BImage* imgs = reinterpret_cast<BImage*>(sl.h_desc + sl.L.imgs);
+  BItem* items = reinterpret_cast<BItem*>(sl.h_desc + sl.L.items);
+  int* starts = reinterpret_cast<int*>(sl.h_desc + sl.L.starts);
+  std::vector<int64_t> tiles(n), cost(n);
+  double total = 0;
+  size_t off = 0;
+  char* abase = static_cast<char*>(sl.arena.p);
+  for (int i = 0; i < n; ++i) {
+    const ImgSpec& sp = specs[i];
+    BImage& im = imgs[i];
+    im.img = sp.d_img;
+    im.n[0] = sp.n[0];
+    im.n[1] = sp.n[1];
+    im.n[2] = sp.n[2];
+    im.bins = sp.bins;
+    im.dtype = sp.dtype;
+    im.smem_hist = sp.bins <= kSmemBinsMax ? 1 : 0;
+    im.tiles_x = (sp.n[2] + kT3X - 1) / kT3X;
+    im.tiles_y = (sp.n[1] + kT3Y - 1) / kT3Y;
+    im.zc = std::min<int64_t>(16, std::max<int64_t>(sp.n[0], 1));
+    const int64_t tz = (sp.n[0] + im.zc - 1) / im.zc;
+    im.vcec = reinterpret_cast<long long*>(abase + off);
+    im.curve = im.vcec + sp.bins;
+    im.err = reinterpret_cast<int*>(im.curve + sp.bins);
+    off += arena_bytes(sp.bins);
+    tiles[i] = sp.n[0] * sp.n[1] * sp.n[2] > 0 ? im.tiles_x * im.tiles_y * tz : 0;
+    cost[i] = (int64_t)kT3X * kT3Y * (im.zc + 2);
+    total += (double)tiles[i] * cost[i];
+  }
+  const double per_block = total / grid;
+  int n_items = 0, b = 0;
+  double acc = 0;
+  starts[0] = 0;
+  for (int i = 0; i < n; ++i) {
+    int64_t t = 0;
+    while (t < tiles[i]) {
+      const double room = per_block * (b + 1) - acc;
+      int64_t k = std::max<int64_t>(1, (int64_t)(room / cost[i] + 0.999));
+      k = std::min(k, tiles[i] - t);
+      if (n_items >= sl.L.item_cap) return set_err(h, ECC_ERR_CUDA, "work list overflow");
+      items[n_items++] = BItem{i, 0, t, t + k};
+      t += k;
+      acc += (double)k * cost[i];
+      while (b < grid - 1 && acc >= per_block * (b + 1) - 1e-9) starts[++b] = n_items;
+    }
+  }
+  while (b < grid) starts[++b] = n_items;
+  // blocks of the launched grid beyond `grid` (the other graph's size) idle
+  for (int j = grid + 1; j <= sl.grid; ++j) starts[j] = n_items;
+  hdr->n_images = n;
+  hdr->n_items = n_items;
+  if (wait_ev && (e = cudaStreamWaitEvent(sl.stream, wait_ev, 0)))
+    return cuda_err(h, e, "wait");
+  (void)wait_on;
+  if ((e = cudaMemcpyAsync(sl.desc.p, sl.h_desc, sl.L.total, cudaMemcpyHostToDevice, sl.stream)))
+    return cuda_err(h, e, "upload work list");
+  cudaGraphExec_t& ex = large ? sl.exec_large : sl.exec_small;
+  if (!ex) {
+    e = h->cfg.convention == kConvT ? capture_graph<kConvT>(sl, large, &ex)
+                                    : capture_graph<kConvV>(sl, large, &ex);
+    if (e) return cuda_err(h, e, "capture batch graph");
+  }
+  if ((e = cudaGraphLaunch(ex, sl.stream))) return cuda_err(h, e, "graph launch");
+  h->launches += 3;
+  if ((e = cudaMemcpyAsync(sl.h_arena, sl.arena.p, arena_total, cudaMemcpyDeviceToHost,
+                           sl.stream)) ||
+      (e = cudaEventRecord(sl.done, sl.stream)))
+    return cuda_err(h, e, "copy results");
+  return ECC_OK;
+}
+
+// Copies image i's curve out of the slot's pinned arena; status from its error word.
+int slot_result(const Slot& sl, const std::vector<ImgSpec>& specs, int i, int64_t** curve) {
+  size_t off = 0;
+  for (int j = 0; j < i; ++j) off += arena_bytes(specs[j].bins);
+  const long long* rec = reinterpret_cast<const long long*>(sl.h_arena + off);
+  const int64_t bins = specs[i].bins;
+  const int err = *reinterpret_cast<const int*>(rec + 2 * bins);
+  if (err & kErrValue) return ECC_ERR_VALUE;
+  if (err & kErrOverflow) return ECC_ERR_CUDA;
+  *curve = static_cast<int64_t*>(std::malloc(sizeof(int64_t) * std::max<int64_t>(bins, 1)));
+  if (!*curve) return ECC_ERR_OOM;
+  std::memcpy(*curve, rec + bins, sizeof(int64_t) * bins);
+  return ECC_OK;
+}
+
+int view3(const int64_t* dims, int ndim, int64_t n[3]) {
+  n[0] = n[1] = n[2] = 1;
+  for (int i = 0; i < ndim; ++i) n[3 - ndim + i] = dims[i];
+  return ECC_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Serving
+// ---------------------------------------------------------------------------
+
+struct Request {
+  enum State { kQueuedHost, kOnDevice, kLaunched, kDone, kFailed, kRetired };
+  uint64_t id = 0;
+  int64_t n[3] = {1, 1, 1};
+  int dtype = kU8;
+  int64_t bins = 256;
+  size_t bytes = 0;
+  std::vector<unsigned char> host_copy;
+  void* d_img = nullptr;
+  State state = kQueuedHost;
+  int status = ECC_OK;
+  int64_t* result = nullptr;
+  int64_t result_bins = 0;
+  std::chrono::steady_clock::time_point t_submit, t_done;
+  int slot = -1;
+};
+
+struct Server {
+  std::mutex mu;
+  std::condition_variable cv;
+  std::thread th;
+  bool stop = false;
+  uint64_t next_id = 1;
+  std::deque<Request*> queue;  // waiting for a launch, FIFO
+  std::map<uint64_t, Request*> all;
+  int64_t bytes_in_use = 0;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copy_ev = nullptr;
+  BatchEngine eng;
+  std::vector<std::vector<Request*>> in_flight;  // per slot
+  std::vector<std::vector<ImgSpec>> specs;       // per slot
+  std::string err;
+};
+
+namespace {
+
+int64_t request_cost(const Request* r) { return (int64_t)r->bytes + (int64_t)arena_bytes(r->bins); }
+
+void free_device_image(Server* sv, Request* r) {
+  if (r->d_img) {
+    cudaFreeAsync(r->d_img, sv->copy_stream);
+    r->d_img = nullptr;
+    sv->bytes_in_use -= request_cost(r);
+  }
+}
+
+// Moves a host-staged request to the device if it fits (caller holds mu).
+bool admit(ecc_handle* h, Server* sv, Request* r) {
+  if (sv->bytes_in_use + request_cost(r) > h->cfg.mem_cap_bytes) return false;
+  void* d = nullptr;
+  cudaError_t e = cudaMallocAsync(&d, std::max<size_t>(r->bytes, 1), sv->copy_stream);
+  if (e) {
+    cudaGetLastError();
+    return false;
+  }
+  if (r->bytes) {
+    e = cudaMemcpyAsync(d, r->host_copy.data(), r->bytes, cudaMemcpyHostToDevice,
+                        sv->copy_stream);
+    if (e) {
+      cudaFreeAsync(d, sv->copy_stream);
+      r->state = Request::kFailed;
+      r->status = ECC_ERR_CUDA;
+      return true;
+    }
+  }
+  r->d_img = d;
+  r->host_copy.clear();
+  r->host_copy.shrink_to_fit();
+  r->state = Request::kOnDevice;
+  sv->bytes_in_use += request_cost(r);
+  return true;
+}
+
+void serve_loop(ecc_handle* h) {
+  Server* sv = h->server;
+  cudaSetDevice(h->device);
+  std::unique_lock<std::mutex> lk(sv->mu);
+  const int nslots = (int)sv->eng.slots.size();
+  while (true) {
+    bool progressed = false;
+    // 1. retire finished batches
+    for (int s = 0; s < nslots; ++s) {
+      auto& fl = sv->in_flight[s];
+      if (fl.empty()) continue;
+      cudaError_t q = cudaEventQuery(sv->eng.slots[s].done);
+      if (q == cudaErrorNotReady) continue;
+      const auto now = std::chrono::steady_clock::now();
+      for (size_t i = 0; i < fl.size(); ++i) {
+        Request* r = fl[i];
+        if (q != cudaSuccess) {
+          r->status = ECC_ERR_CUDA;
+        } else {
+          r->status = slot_result(sv->eng.slots[s], sv->specs[s], (int)i, &r->result);
+          r->result_bins = r->bins;
+        }
+        r->state = r->status == ECC_OK ? Request::kDone : Request::kFailed;
+        r->t_done = now;
+        free_device_image(sv, r);
+      }
+      if (q != cudaSuccess) cudaGetLastError();
+      fl.clear();
+      progressed = true;
+    }
+    if (sv->stop) break;
+    // 2. admit host-staged requests in arrival order while memory allows
+    for (Request* r : sv->queue) {
+      if (r->state != Request::kQueuedHost) continue;
+      if (!admit(h, sv, r)) break;
+      progressed = true;
+    }
+    // 3. launch the admitted requests on a free slot
+    int free_slot = -1;
+    for (int s = 0; s < nslots; ++s)
+      if (sv->in_flight[s].empty()) {
+        free_slot = s;
+        break;
+      }
+    if (free_slot >= 0) {
+      std::vector<Request*> batch;
+      std::vector<ImgSpec> specs;
+      for (auto it = sv->queue.begin(); it != sv->queue.end() && (int)batch.size() < kMaxBatch;) {
+        Request* r = *it;
+        if (r->state == Request::kFailed) {
+          it = sv->queue.erase(it);
+          continue;
+        }
+        if (r->state != Request::kOnDevice) {
+          ++it;
+          continue;
+        }
+        batch.push_back(r);
+        specs.push_back(ImgSpec{r->d_img, {r->n[0], r->n[1], r->n[2]}, r->dtype, r->bins});
+        it = sv->queue.erase(it);
+      }
+      if (!batch.empty()) {
+        Slot& sl = sv->eng.slots[free_slot];
+        cudaEventRecord(sv->copy_ev, sv->copy_stream);  // all admitted copies
+        int rc = slot_run(h, sl, specs, sv->copy_stream, sv->copy_ev);
+        for (Request* r : batch) {
+          r->slot = free_slot;
+          r->state = Request::kLaunched;
+        }
+        if (rc) {
+          for (Request* r : batch) {
+            r->state = Request::kFailed;
+            r->status = rc;
+            r->t_done = std::chrono::steady_clock::now();
+            free_device_image(sv, r);
+          }
+        } else {
+          sv->in_flight[free_slot] = batch;
+          sv->specs[free_slot] = specs;
+        }
+        progressed = true;
+      }
+    }
+    if (progressed) {
+      sv->cv.notify_all();
+      continue;
+    }
+    bool busy = false;
+    for (int s = 0; s < nslots; ++s) busy = busy || !sv->in_flight[s].empty();
+    if (busy)
+      sv->cv.wait_for(lk, std::chrono::microseconds(20));
+    else
+      sv->cv.wait_for(lk, std::chrono::milliseconds(5));
+  }
+}
+
+int server_start(ecc_handle* h) {
+  if (h->server) return ECC_OK;
+  Server* sv = new (std::nothrow) Server();
+  if (!sv) return set_err(h, ECC_ERR_OOM, "server");
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&sv->copy_stream, cudaStreamNonBlocking)) ||
+      (e = cudaEventCreateWithFlags(&sv->copy_ev, cudaEventDisableTiming))) {
+    delete sv;
+    return cuda_err(h, e, "server streams");
+  }
+  sv->eng.slots.resize(2);
+  for (Slot& sl : sv->eng.slots) {
+    int rc = slot_init(h, sl);
+    if (rc) {
+      for (Slot& s2 : sv->eng.slots) slot_free(s2);
+      delete sv;
+      return rc;
+    }
+  }
+  sv->in_flight.resize(2);
+  sv->specs.resize(2);
+  // keep freed stream-ordered allocations cached in the pool
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, h->device) == cudaSuccess) {
+    uint64_t thr = (uint64_t)h->cfg.mem_cap_bytes;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  h->server = sv;
+  sv->th = std::thread(serve_loop, h);
+  return ECC_OK;
+}
+
+}  // namespace
+
+void serve_shutdown(ecc_handle* h) {
+  if (h->server) {
+    Server* sv = h->server;
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      sv->stop = true;
+    }
+    sv->cv.notify_all();
+    if (sv->th.joinable()) sv->th.join();
+    cudaSetDevice(h->device);
+    for (Slot& sl : sv->eng.slots) slot_free(sl);
+    for (auto& kv : sv->all) {
+      Request* r = kv.second;
+      if (r->d_img) cudaFreeAsync(r->d_img, sv->copy_stream);
+      std::free(r->result);
+      delete r;
+    }
+    cudaStreamSynchronize(sv->copy_stream);
+    cudaEventDestroy(sv->copy_ev);
+    cudaStreamDestroy(sv->copy_stream);
+    delete sv;
+    h->server = nullptr;
+  }
+  if (h->batch) {
+    for (Slot& sl : h->batch->slots) slot_free(sl);
+    delete h->batch;
+    h->batch = nullptr;
+  }
+}
+
 }  // namespace ecc
 
 using namespace ecc;
 
 extern "C" {
-int ecc_compute_batch(ecc_handle* h, int, const ecc_image*, ecc_result*) {
-  return set_err(h, ECC_ERR_STATE, "batched computation not built yet");
+
+int ecc_compute_batch(ecc_handle* h, int n, const ecc_image* images, ecc_result* outs) {
+  if (!h) return ECC_ERR_ARG;
+  try {
+    std::lock_guard<std::mutex> lk(h->api_mu);
+    h->err.clear();
+    if (n < 0 || (n > 0 && (!images || !outs))) return set_err(h, ECC_ERR_ARG, "bad batch");
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e) return cuda_err(h, e, "set device");
+    for (int i = 0; i < n; ++i) {
+      std::memset(&outs[i], 0, sizeof(ecc_result));
+      outs[i].owned = 1;
+    }
+    if (!h->batch) {
+      h->batch = new BatchEngine();
+      h->batch->slots.resize(1);
+      int rc = slot_init(h, h->batch->slots[0]);
+      if (rc) {
+        slot_free(h->batch->slots[0]);
+        delete h->batch;
+        h->batch = nullptr;
+        return rc;
+      }
+    }
+    Slot& sl = h->batch->slots[0];
+    // validate, stage host images into one device buffer
+    std::vector<ImgSpec> all(n);
+    std::vector<int> ok(n, 0);
+    std::vector<size_t> host_off(n, SIZE_MAX);
+    size_t staged = 0;
+    for (int i = 0; i < n; ++i) {
+      const ecc_image& im = images[i];
+      Shape s;
+      int rc = validate_shape(h, im.dims, im.ndim, &s);
+      if (rc == ECC_OK && im.ndim > 3) rc = set_err(h, ECC_ERR_ARG, "batched images are 1-3D");
+      if (rc == ECC_OK && im.dtype != ECC_U8 && im.dtype != ECC_U16)
+        rc = set_err(h, ECC_ERR_DTYPE, "batched images are ECC_U8 or ECC_U16");
+      const int64_t bins = im.bins > 0 ? im.bins : default_bins(h, im.dtype);
+      if (rc == ECC_OK && (bins > (int64_t(1) << 24))) rc = set_err(h, ECC_ERR_ARG, "bins");
+      if (rc == ECC_OK && s.voxels > 0 && !im.data) rc = set_err(h, ECC_ERR_ARG, "null image");
+      outs[i].status = rc;
+      if (rc) continue;
+      ok[i] = 1;
+      all[i].dtype = im.dtype;
+      all[i].bins = bins;
+      view3(im.dims, im.ndim, all[i].n);
+      all[i].d_img = im.data;
+      if (s.voxels > 0 && !is_device_ptr(h, im.data)) {
+        host_off[i] = staged;
+        staged += (dtype_bytes(im.dtype) * s.voxels + 255) & ~size_t(255);
+      }
+    }
+    if (staged) {
+      if ((e = h->img.ensure(staged))) return cuda_err(h, e, "batch staging");
+      for (int i = 0; i < n; ++i) {
+        if (host_off[i] == SIZE_MAX) continue;
+        const size_t bytes = dtype_bytes(all[i].dtype) * all[i].n[0] * all[i].n[1] * all[i].n[2];
+        char* d = static_cast<char*>(h->img.p) + host_off[i];
+        if ((e = cudaMemcpyAsync(d, images[i].data, bytes, cudaMemcpyHostToDevice, sl.stream)))
+          return cuda_err(h, e, "copy batch image");
+        all[i].d_img = d;
+      }
+    }
+    // run in chunks of kMaxBatch valid images
+    std::vector<int> idx;
+    for (int i = 0; i < n; ++i)
+      if (ok[i]) idx.push_back(i);
+    for (size_t c0 = 0; c0 < idx.size(); c0 += kMaxBatch) {
+      const size_t c1 = std::min(idx.size(), c0 + kMaxBatch);
+      std::vector<ImgSpec> specs;
+      for (size_t j = c0; j < c1; ++j) specs.push_back(all[idx[j]]);
+      int rc = slot_run(h, sl, specs, nullptr, nullptr);
+      if (!rc) rc = wait_event(h, sl.done, 300LL * 1000 * 1000);
+      if (rc) return rc;
+      for (size_t j = c0; j < c1; ++j) {
+        ecc_result& o = outs[idx[j]];
+        o.status = slot_result(sl, specs, (int)(j - c0), &o.curve);
+        o.bins = o.status == ECC_OK ? specs[j - c0].bins : 0;
+      }
+    }
+    return ECC_OK;
+  } catch (const std::bad_alloc&) {
+    return set_err(h, ECC_ERR_OOM, "host allocation");
+  } catch (...) {
+    return set_err(h, ECC_ERR_CUDA, "internal error");
+  }
 }
-int ecc_submit(ecc_handle* h, const void*, const int64_t*, int, ecc_dtype, uint64_t*) {
-  return set_err(h, ECC_ERR_STATE, "serving not built yet");
+
+int ecc_submit(ecc_handle* h, const void* image, const int64_t* dims, int ndim, ecc_dtype dtype,
+               uint64_t* req_id) {
+  if (!h) return ECC_ERR_ARG;
+  try {
+    Shape s;
+    {
+      std::lock_guard<std::mutex> lk(h->api_mu);
+      h->err.clear();
+      if (!req_id) return set_err(h, ECC_ERR_ARG, "req_id is NULL");
+      int rc = validate_shape(h, dims, ndim, &s);
+      if (rc) return rc;
+      if (ndim > 3) return set_err(h, ECC_ERR_ARG, "served images are 1-3D");
+      if (dtype != ECC_U8 && dtype != ECC_U16)
+        return set_err(h, ECC_ERR_DTYPE, "served images are ECC_U8 or ECC_U16");
+      if (s.voxels > 0 && !image) return set_err(h, ECC_ERR_ARG, "image is NULL");
+      cudaError_t e = cudaSetDevice(h->device);
+      if (e) return cuda_err(h, e, "set device");
+      rc = server_start(h);
+      if (rc) return rc;
+    }
+    Server* sv = h->server;
+    Request* r = new Request();
+    r->dtype = dtype;
+    r->bins = default_bins(h, dtype);
+    view3(dims, ndim, r->n);
+    r->bytes = dtype_bytes(dtype) * (size_t)s.voxels;
+    r->t_submit = std::chrono::steady_clock::now();
+    if (request_cost(r) > h->cfg.mem_cap_bytes) {
+      delete r;
+      return set_err(h, ECC_ERR_OOM, "request larger than the device memory cap");
+    }
+    // the caller's buffer is copied before returning: into a host copy; the
+    // scheduler moves it to the device when memory is available
+    r->host_copy.resize(r->bytes);
+    if (r->bytes) std::memcpy(r->host_copy.data(), image, r->bytes);
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      r->id = sv->next_id++;
+      sv->all[r->id] = r;
+      admit(h, sv, r);
+      sv->queue.push_back(r);
+      *req_id = r->id;
+    }
+    sv->cv.notify_all();
+    return ECC_OK;
+  } catch (const std::bad_alloc&) {
+    return set_err(h, ECC_ERR_OOM, "host allocation");
+  } catch (...) {
+    return set_err(h, ECC_ERR_CUDA, "internal error");
+  }
 }
-int ecc_poll(ecc_handle* h, uint64_t, ecc_result*, int64_t) {
-  return set_err(h, ECC_ERR_STATE, "serving not built yet");
+
+int ecc_poll(ecc_handle* h, uint64_t req_id, ecc_result* out, int64_t timeout_us) {
+  if (!h || !out) return ECC_ERR_ARG;
+  Server* sv = h->server;
+  if (!sv) return ECC_ERR_ARG;
+  std::unique_lock<std::mutex> lk(sv->mu);
+  auto it = sv->all.find(req_id);
+  if (it == sv->all.end() || it->second->state == Request::kRetired) return ECC_ERR_ARG;
+  Request* r = it->second;
+  auto finished = [&] { return r->state == Request::kDone || r->state == Request::kFailed; };
+  if (!finished()) {
+    if (timeout_us == 0) return ECC_PENDING;
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(timeout_us);
+    if (!sv->cv.wait_until(lk, deadline, finished)) return ECC_ERR_TIMEOUT;
+  }
+  std::memset(out, 0, sizeof *out);
+  out->status = r->status;
+  const int rc = r->status;
+  if (rc == ECC_OK) {
+    out->owned = 1;
+    out->bins = r->result_bins;
+    out->curve = r->result;
+    r->result = nullptr;
+  }
+  r->state = Request::kRetired;
+  return rc;
 }
-int ecc_request_latency_us(ecc_handle* h, uint64_t, double*) {
-  return set_err(h, ECC_ERR_STATE, "serving not built yet");
+
+int ecc_request_latency_us(ecc_handle* h, uint64_t req_id, double* us) {
+  if (!h || !us || !h->server) return ECC_ERR_ARG;
+  Server* sv = h->server;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->all.find(req_id);
+  if (it == sv->all.end()) return ECC_ERR_ARG;
+  Request* r = it->second;
+  if (r->state != Request::kDone && r->state != Request::kRetired && r->state != Request::kFailed)
+    return ECC_ERR_ARG;
+  *us = std::chrono::duration<double, std::micro>(r->t_done - r->t_submit).count();
+  return ECC_OK;
 }
-}
+
+}  // extern "C"

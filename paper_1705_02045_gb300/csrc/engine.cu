@@ -83,7 +83,17 @@ bool is_device_ptr(const ecc_handle* h, const void* p) {
          at.device == h->device;
 }
 
+cudaError_t launch_local_bits(const LocalArgs& a, int num_sms, int64_t* launches);
+
+// Kernel choice: the bit-sliced kernel where it applies (1-3D integer images
+// with 256, 16384 or 65536 bins and 16-byte aligned rows), the generic kernel
+// otherwise. variant 1 forces the generic kernel, 2 the bit-sliced one.
 cudaError_t launch_local(const LocalArgs& a, int num_sms, int64_t* launches) {
+  if (a.variant != 1) {
+    cudaError_t e = launch_local_bits(a, num_sms, launches);
+    if (e != cudaErrorNotSupported || a.variant == 2) return e;
+    cudaGetLastError();
+  }
   return launch_local_generic(a, num_sms, launches);
 }
 
@@ -110,6 +120,7 @@ int enqueue_int(ecc_handle* h, const void* d_img, const Shape& s, int dtype, int
     a.view = s.view;
     for (int i = 0; i < 4; ++i) a.n[i] = s.n[i];
     a.bins = bins;
+    a.variant = h->variant;
     a.vcec = d_vcec;
     a.err = h->errw.as<int>();
     a.stream = stream;
@@ -295,6 +306,10 @@ int ecc_create(const ecc_config* cfg, ecc_handle** out) {
   if (h->cfg.ring_bytes == 0) h->cfg.ring_bytes = int64_t(4) << 30;
   if (h->cfg.mem_cap_bytes == 0) h->cfg.mem_cap_bytes = int64_t(32) << 30;
   h->device = h->cfg.device;
+  if (const char* kv = std::getenv("ECC_KERNEL")) {
+    if (!std::strcmp(kv, "generic")) h->variant = 1;
+    else if (!std::strcmp(kv, "bits")) h->variant = 2;
+  }
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess || h->device < 0 || h->device >= ndev) {

@@ -50,7 +50,8 @@ struct Shape {
   int64_t n[4] = {1, 1, 1, 1};
 };
 
-struct Request;  // serving (batch.cu)
+struct BatchEngine;  // batch.cu
+struct Server;       // batch.cu
 
 }  // namespace ecc
 
@@ -58,6 +59,7 @@ struct ecc_handle {
   ecc_config cfg{};
   int device = 0;
   int num_sms = 0;
+  int variant = 0;                     // contribution kernel: 0 auto, 1 generic, 2 bit-sliced
   cudaStream_t stream = nullptr;       // compute
   cudaStream_t copy_stream = nullptr;  // host <-> device
   std::string err;
@@ -73,18 +75,9 @@ struct ecc_handle {
   bool prof_on = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
 
-  // serving state (batch.cu)
-  std::mutex sv_mu;
-  std::condition_variable sv_cv;
-  std::thread sv_thread;
-  bool sv_stop = false;
-  bool sv_started = false;
-  uint64_t sv_next_id = 1;
-  std::deque<ecc::Request*> sv_queue;
-  std::map<uint64_t, ecc::Request*> sv_all;
-  int64_t sv_bytes_in_use = 0;
-  cudaStream_t sv_stream = nullptr;
-  cudaStream_t sv_copy_stream = nullptr;
+  // batched launches and serving (batch.cu)
+  ecc::BatchEngine* batch = nullptr;   // used by ecc_compute_batch
+  ecc::Server* server = nullptr;       // request loop of ecc_submit / ecc_poll
 };
 
 namespace ecc {

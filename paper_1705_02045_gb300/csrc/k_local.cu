@@ -9,8 +9,7 @@
 // voxel is read from global memory once per tile plus the one-voxel collar of
 // Sec. 3 ("Processing one Chunk"). Outside voxels are +inf (Sec. 4,
 // limitations: the second collar of infinite voxels), here by a bounds test.
-#include "ecc_device.cuh"
-#include "ecc_internal.h"
+#include "ecc_tile.cuh"
 
 #include <algorithm>
 
@@ -18,63 +17,11 @@ namespace ecc {
 
 namespace {
 
-constexpr int kThreads = 256;
-enum Mode : int { kSmemHist = 0, kGlobalHist = 1, kPairs = 2 };
-
-// G_2 straight from its definition: sum over delta in {-1,0,1}^2 of
-// (-1)^{nz(delta)} times [all bits of the box B_delta set].
-__device__ int g2_entry(uint32_t m) {
-  int g = 0;
-  for (int dy = -1; dy <= 1; ++dy)
-    for (int dx = -1; dx <= 1; ++dx) {
-      bool all = true;
-      for (int ey = 0; ey <= (dy != 0 ? 1 : 0); ++ey)
-        for (int ex = 0; ex <= (dx != 0 ? 1 : 0); ++ex) {
-          if (ey == 0 && ex == 0) continue;
-          all = all && ((m >> ring_pos(ey * dy, ex * dx)) & 1u);
-        }
-      if (all) g += ((dy != 0) + (dx != 0)) & 1 ? -1 : 1;
-    }
-  return g;
-}
-
-template <typename T>
-__device__ __forceinline__ uint32_t load_key(const T* base, int64_t off, int* err) {
-  const T v = base[off];
-  if (value_bad(v)) atomicOr(err, kErrValue);
-  return value_key(v);
-}
-
-// Accumulates one change into the selected output.
-template <int MODE>
-__device__ __forceinline__ void deposit(bool valid, uint32_t kv, int c, int* hist,
-                                        const LocalArgs& a) {
-  if (MODE == kPairs) {
-    emit_pair(valid && c != 0, kv, c, a.pairs, a.pair_count, a.pair_cap, a.err);
-    return;
-  }
-  if (!valid || c == 0) return;
-  if ((int64_t)kv >= a.bins) {
-    atomicOr(a.err, kErrValue);
-    return;
-  }
-  if (MODE == kSmemHist)
-    atomicAdd(&hist[kv], c);
-  else
-    atomicAdd(reinterpret_cast<unsigned long long*>(a.vcec) + kv,
-              (unsigned long long)(long long)c);
-}
+constexpr int kThreads = kTileThreads;
 
 template <int MODE>
-__device__ void flush_hist(int* hist, const LocalArgs& a) {
-  if (MODE != kSmemHist) return;
-  __syncthreads();
-  for (int64_t b = threadIdx.x; b < a.bins; b += kThreads) {
-    const int v = hist[b];
-    if (v != 0)
-      atomicAdd(reinterpret_cast<unsigned long long*>(a.vcec) + b,
-                (unsigned long long)(long long)v);
-  }
+__device__ void flush_hist(const Sink& s) {
+  if (MODE == kSmemHist) flush_smem_hist(s);
 }
 
 // ---------------------------------------------------------------------------
@@ -83,81 +30,30 @@ __device__ void flush_hist(int* hist, const LocalArgs& a) {
 template <typename T, int CONV, int MODE>
 __global__ void __launch_bounds__(kThreads)
 k_local3(const LocalArgs a, int64_t zc, int64_t tiles_x, int64_t tiles_y, int64_t n_tiles) {
-  constexpr int TX = 32, TY = 8, PW = TX + 2, PH = TY + 2, PL = PW * PH;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* ring = reinterpret_cast<uint32_t*>(smem);
-  int8_t* g2 = reinterpret_cast<int8_t*>(ring + 4 * PL);
-  int* hist = reinterpret_cast<int*>(g2 + 256);
-
-  const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
-  g2[tid] = (int8_t)g2_entry(tid);
-  if (MODE == kSmemHist)
-    for (int64_t b = tid; b < a.bins; b += kThreads) hist[b] = 0;
+  int8_t* g2 = reinterpret_cast<int8_t*>(ring + 4 * kT3PL);
+  Sink s;
+  s.bins = a.bins;
+  s.vcec = a.vcec;
+  s.hist = reinterpret_cast<int*>(g2 + 256);
+  s.err = a.err;
+  s.pairs = a.pairs;
+  s.pair_count = a.pair_count;
+  s.pair_cap = a.pair_cap;
+  g2[threadIdx.x] = (int8_t)g2_entry(threadIdx.x);
+  if (MODE == kSmemHist) clear_smem_hist(s);
   __syncthreads();
-
   const T* img = static_cast<const T*>(a.img);
-  const int64_t nz = a.n[0], ny = a.n[1], nx = a.n[2];
-  const int64_t plane = ny * nx;
-
   for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     const int64_t txy = tiles_x * tiles_y;
     const int64_t tz = t / txy, rem = t - tz * txy;
-    const int64_t y0 = (rem / tiles_x) * TY, x0 = (rem % tiles_x) * TX;
+    const int64_t y0 = (rem / tiles_x) * kT3Y, x0 = (rem % tiles_x) * kT3X;
     const int64_t z0 = a.w_lo + tz * zc, z1 = min(z0 + zc, a.w_hi);
-
-    auto load_plane = [&](int64_t zp) {
-      uint32_t* dst = ring + (int)(zp & 3) * PL;
-      for (int i = tid; i < PL; i += kThreads) {
-        const int ly = i / PW, lx = i - ly * PW;
-        const int64_t gy = y0 + ly - 1, gx = x0 + lx - 1;
-        uint32_t key = kOutside;
-        if (zp >= 0 && zp < nz && gy >= 0 && gy < ny && gx >= 0 && gx < nx) {
-          if (zp >= a.w_mem_lo && zp < a.w_mem_hi)
-            key = load_key(img, (zp - a.w_mem_lo) * plane + gy * nx + gx, a.err);
-          else
-            atomicOr(a.err, kErrOverflow);  // plane needed but not resident
-        }
-        dst[i] = key;
-      }
-    };
-
-    load_plane(z0 - 1);
-    load_plane(z0);
-    load_plane(z0 + 1);
-    __syncthreads();
-
-    const int64_t gx = x0 + tx, gy = y0 + ty;
-    const bool valid = gx < nx && gy < ny;
-    for (int64_t z = z0; z < z1; ++z) {
-      if (z + 2 <= z1) load_plane(z + 2);
-      const uint32_t* pm = ring + (int)((z - 1) & 3) * PL;
-      const uint32_t* p0 = ring + (int)(z & 3) * PL;
-      const uint32_t* pp = ring + (int)((z + 1) & 3) * PL;
-      const int c0 = (ty + 1) * PW + tx + 1;
-      const uint32_t kv = p0[c0];
-      uint32_t m = 0;
-#pragma unroll
-      for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-          if (dy == 0 && dx == 0) continue;
-          const int o = c0 + dy * PW + dx;
-          const int r = ring_pos(dy, dx);
-          const bool fwd = dy > 0 || (dy == 0 && dx > 0);
-          m |= (fwd ? after<true>(p0[o], kv) : after<false>(p0[o], kv)) << r;
-          m |= after<true>(pp[o], kv) << (8 + r);
-          m |= after<false>(pm[o], kv) << (16 + r);
-        }
-      m |= after<true>(pp[c0], kv) << 24;
-      m |= after<false>(pm[c0], kv) << 25;
-      if (CONV == kConvT) m = ~m & 0x3FFFFFFu;
-      const int g = g3_of_mask(m, g2);
-      const int c = CONV == kConvV ? -g : g;
-      deposit<MODE>(valid, kv, c, hist, a);
-      __syncthreads();
-    }
+    run_tile3<T, CONV, MODE>(img, a.n[0], a.n[1], a.n[2], a.w_mem_lo, a.w_mem_hi, x0, y0, z0,
+                             z1, ring, g2, s);
   }
-  flush_hist<MODE>(hist, a);
+  flush_hist<MODE>(s);
 }
 
 // ---------------------------------------------------------------------------
@@ -172,12 +68,18 @@ k_local4(const LocalArgs a, int64_t wc, int64_t tiles_x, int64_t tiles_y, int64_
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* ring = reinterpret_cast<uint32_t*>(smem);
   int8_t* g2 = reinterpret_cast<int8_t*>(ring + 4 * PL);
-  int* hist = reinterpret_cast<int*>(g2 + 256);
+  Sink s;
+  s.bins = a.bins;
+  s.vcec = a.vcec;
+  s.hist = reinterpret_cast<int*>(g2 + 256);
+  s.err = a.err;
+  s.pairs = a.pairs;
+  s.pair_count = a.pair_count;
+  s.pair_cap = a.pair_cap;
 
   const int tid = threadIdx.x, tx = tid % TX, ty = (tid / TX) % TY, tz = tid / (TX * TY);
   g2[tid] = (int8_t)g2_entry(tid);
-  if (MODE == kSmemHist)
-    for (int64_t b = tid; b < a.bins; b += kThreads) hist[b] = 0;
+  if (MODE == kSmemHist) clear_smem_hist(s);
   __syncthreads();
 
   const T* img = static_cast<const T*>(a.img);
@@ -251,11 +153,11 @@ k_local4(const LocalArgs a, int64_t wc, int64_t tiles_x, int64_t tiles_y, int64_
       if (bp) g -= g3_of_mask(M0 & Mp, g2);
       if (bm) g -= g3_of_mask(M0 & Mm, g2);
       const int c = g;  // (-1)^4 G_4 for V; G_4 of the complement for T
-      deposit<MODE>(valid, kv, c, hist, a);
+      deposit<MODE>(valid, kv, c, s);
       __syncthreads();
     }
   }
-  flush_hist<MODE>(hist, a);
+  flush_hist<MODE>(s);
 }
 
 template <typename T, int CONV, int MODE>
@@ -264,8 +166,7 @@ cudaError_t launch_typed(const LocalArgs& a, int num_sms, int64_t* launches) {
   if (wn <= 0) return cudaSuccess;
   size_t hist_bytes = MODE == kSmemHist ? (size_t)a.bins * sizeof(int) : 0;
   if (a.view == 3) {
-    constexpr int PL = 34 * 10;
-    const size_t smem = 4 * PL * 4 + 256 + hist_bytes;
+    const size_t smem = 4 * kT3PL * 4 + 256 + hist_bytes;
     auto kern = k_local3<T, CONV, MODE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);

@@ -18,7 +18,7 @@
 
 namespace ecc {
 
-struct Slot {
+struct StreamSlot {
   cudaEvent_t copied = nullptr;  // host planes landed in the slot
   cudaEvent_t freed = nullptr;   // contribution kernel on this slot finished
   int64_t z0 = 0, nz = 0;
@@ -38,7 +38,7 @@ struct ecc_stream {
   int64_t depth = 64;
   int R = 0;
   DevBuf ring, vcec, curve;
-  std::vector<Slot> slots;
+  std::vector<StreamSlot> slots;
   int64_t next_z = 0;
   int64_t chunks = 0;
   int pending = -1;  // slot whose kernel waits for the next chunk's first plane
@@ -55,7 +55,7 @@ char* slot_base(ecc_stream* st, int k) {
 // readable from the slot (the collar planes outside the image are never read).
 int launch_slot(ecc_stream* st, int k, bool has_upper) {
   ecc_handle* h = st->h;
-  Slot& sl = st->slots[k];
+  StreamSlot& sl = st->slots[k];
   LocalArgs a;
   a.img = slot_base(st, k);
   a.dtype = st->dtype;
@@ -67,6 +67,7 @@ int launch_slot(ecc_stream* st, int k, bool has_upper) {
   a.w_mem_lo = sl.z0 - 1;
   a.w_mem_hi = sl.z0 + sl.nz + (has_upper ? 1 : 0);
   a.bins = st->bins;
+  a.variant = h->variant;
   a.vcec = st->vcec.as<long long>();
   a.err = h->errw.as<int>();
   a.stream = h->stream;
@@ -85,7 +86,7 @@ void release(ecc_stream* st) {
     cudaStreamSynchronize(st->h->stream);
     cudaStreamSynchronize(st->h->copy_stream);
   }
-  for (Slot& sl : st->slots) {
+  for (StreamSlot& sl : st->slots) {
     if (sl.copied) cudaEventDestroy(sl.copied);
     if (sl.freed) cudaEventDestroy(sl.freed);
   }
@@ -153,7 +154,7 @@ int ecc_stream_begin(ecc_handle* h, const int64_t* dims, int ndim, ecc_dtype dty
       release(st);
       return cuda_err(h, e, "stream buffers");
     }
-    for (Slot& sl : st->slots) {
+    for (StreamSlot& sl : st->slots) {
       if ((e = cudaEventCreateWithFlags(&sl.copied, cudaEventDisableTiming)) ||
           (e = cudaEventCreateWithFlags(&sl.freed, cudaEventDisableTiming))) {
         release(st);
@@ -195,7 +196,7 @@ int ecc_stream_push_slab(ecc_stream* st, const void* host_planes, int64_t z0, in
     for (int64_t off = 0; off < nz; off += st->depth) {
       const int64_t cnz = std::min<int64_t>(st->depth, nz - off);
       const int k = (int)(st->chunks % st->R);
-      Slot& sl = st->slots[k];
+      StreamSlot& sl = st->slots[k];
       char* base = slot_base(st, k);
       if (sl.used && (e = cudaStreamWaitEvent(h->copy_stream, sl.freed, 0))) break;
       if ((e = cudaMemcpyAsync(base + st->plane_bytes, src + off * st->plane_bytes,
@@ -208,7 +209,7 @@ int ecc_stream_push_slab(ecc_stream* st, const void* host_planes, int64_t z0, in
       sl.used = true;
       if (st->pending >= 0) {
         const int p = st->pending;
-        Slot& ps = st->slots[p];
+        StreamSlot& ps = st->slots[p];
         char* pbase = slot_base(st, p);
         // collars: our first plane above the previous chunk, its last below ours
         if ((e = cudaMemcpyAsync(pbase + (ps.nz + 1) * st->plane_bytes, base + st->plane_bytes,

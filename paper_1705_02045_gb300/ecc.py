@@ -102,8 +102,13 @@ def load(build_if_missing: bool = False):
 
 
 def _dtype_code(dt) -> int:
-    name = str(dt).replace("torch.", "")
-    return {"uint8": ECC_U8, "uint16": ECC_U16, "float32": ECC_F32}[name]
+    """ECC dtype code of a numpy dtype / scalar type or a torch dtype; other
+    types map to 0, which the library rejects with ECC_ERR_DTYPE."""
+    try:
+        name = np.dtype(dt).name
+    except TypeError:
+        name = str(dt).replace("torch.", "")
+    return {"uint8": ECC_U8, "uint16": ECC_U16, "float32": ECC_F32}.get(name, 0)
 
 
 def _check(h, rc: int) -> int:

@@ -1,0 +1,270 @@
+"""GPU parity of the streamed, batched and served paths against the CPU oracle,
+and their host-side error handling (wrong slab order, missing planes, values
+out of range, unknown requests, a memory cap smaller than the request mix)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1705_02045_gb300 import ecc, synth
+
+pytestmark = pytest.mark.gpu
+
+S = synth.SEED_BASE + 500
+
+
+def _push_all(h, s, img, sizes):
+    z = 0
+    for n in sizes:
+        ecc.ecc_stream_push_slab(h, s, img[z:z + n], z)
+        z += n
+    assert z == img.shape[0]
+
+
+# ---- streaming --------------------------------------------------------------
+
+@pytest.mark.parametrize("conv", [0, 1])
+def test_stream_3d_u8_uneven_slabs_small_ring(lib, conv):
+    img = synth.smooth_u8((40, 33, 37), 1.5, S + 1)
+    plane = 33 * 37
+    # ring of 13 planes: 2 slots of depth 4 (+2 collar planes each)
+    h = ecc.ecc_create(device=0, slab_depth=4, ring_bytes=13 * plane, convention=conv)
+    try:
+        s = ecc.ecc_stream_begin(h, img.shape, img.dtype)
+        _push_all(h, s, img, [1, 5, 3, 9, 22])
+        got = ecc.ecc_stream_finish(h, s)
+    finally:
+        ecc.ecc_destroy(h)
+    assert np.array_equal(got, oracle.ecc_int(img, 256, "V" if conv == 0 else "T"))
+
+
+def test_stream_4d_u16_14bit(lib):
+    img = synth.two_phase_u16((12, 5, 6, 7), 1.5, S + 2)
+    h = ecc.ecc_create(device=0, slab_depth=3, bins=16384)
+    try:
+        s = ecc.ecc_stream_begin(h, img.shape, img.dtype)
+        _push_all(h, s, img, [2, 2, 7, 1])
+        got = ecc.ecc_stream_finish(h, s)
+    finally:
+        ecc.ecc_destroy(h)
+    assert np.array_equal(got, oracle.ecc_int(img, 16384, "V"))
+
+
+@pytest.mark.parametrize("shape", [(50, 70), (31,)], ids=str)
+def test_stream_1d_2d(lib, shape):
+    img = synth.uniform_u8(shape, S + 3)
+    h = ecc.ecc_create(device=0, slab_depth=8)
+    try:
+        s = ecc.ecc_stream_begin(h, img.shape, img.dtype)
+        _push_all(h, s, img, [shape[0] // 3, shape[0] - shape[0] // 3])
+        got = ecc.ecc_stream_finish(h, s)
+    finally:
+        ecc.ecc_destroy(h)
+    assert np.array_equal(got, oracle.ecc_int(img, 256, "V"))
+
+
+def test_stream_equals_resident_larger(lib):
+    """Streamed in slabs of 16 through a 3-slot ring == resident, bit for bit."""
+    img = synth.two_phase_u16((100, 160, 144), 3.0, S + 4)
+    h = ecc.ecc_create(device=0, slab_depth=16, bins=16384)
+    try:
+        resident = ecc.ecc_compute(h, img)
+        s = ecc.ecc_stream_begin(h, img.shape, img.dtype)
+        _push_all(h, s, img, [37, 37, 26])
+        streamed = ecc.ecc_stream_finish(h, s)
+    finally:
+        ecc.ecc_destroy(h)
+    assert np.array_equal(streamed, resident)
+    assert resident[-1] == 1
+    sub = img[:, :40, :50]
+    assert np.array_equal(ecc_sub(sub), oracle.ecc_int(sub, 16384, "V"))
+
+
+def ecc_sub(sub):
+    h = ecc.ecc_create(device=0, bins=16384)
+    try:
+        return ecc.ecc_compute(h, np.ascontiguousarray(sub))
+    finally:
+        ecc.ecc_destroy(h)
+
+
+def test_stream_pinned_host_buffer(lib):
+    import torch
+    img = synth.smooth_u8((20, 64, 64), 2.0, S + 5)
+    h = ecc.ecc_create(device=0, slab_depth=5)
+    try:
+        s = ecc.ecc_stream_begin(h, img.shape, img.dtype)
+        buf = torch.empty((5, 64, 64), dtype=torch.uint8).pin_memory()
+        for z in range(0, 20, 5):
+            buf.copy_(torch.from_numpy(img[z:z + 5]))
+            ecc.ecc_stream_push_slab(h, s, buf, z)  # buffer reused right after
+        got = ecc.ecc_stream_finish(h, s)
+    finally:
+        ecc.ecc_destroy(h)
+    assert np.array_equal(got, oracle.ecc_int(img, 256, "V"))
+
+
+def test_stream_errors(lib):
+    img = synth.uniform_u8((10, 8, 8), S + 6)
+    h = ecc.ecc_create(device=0, slab_depth=4)
+    try:
+        s = ecc.ecc_stream_begin(h, img.shape, img.dtype)
+        with pytest.raises(ecc.EccError) as ei:
+            ecc.ecc_stream_push_slab(h, s, img[3:5], 3)  # not the next plane
+        assert ei.value.status == ecc.ECC_ERR_STATE
+        ecc.ecc_stream_push_slab(h, s, img[0:4], 0)
+        with pytest.raises(ecc.EccError) as ei:
+            ecc.ecc_stream_finish(h, s)  # planes 4..9 missing
+        assert ei.value.status == ecc.ECC_ERR_STATE
+        # the handle still works, and a value error is reported at finish
+        h2 = ecc.ecc_create(device=0, bins=100)
+        try:
+            s2 = ecc.ecc_stream_begin(h2, img.shape, img.dtype)
+            bad = img.copy()
+            bad[7, 3, 3] = 200
+            _push_all(h2, s2, bad, [5, 5])
+            with pytest.raises(ecc.EccError) as ei:
+                ecc.ecc_stream_finish(h2, s2)
+            assert ei.value.status == ecc.ECC_ERR_VALUE
+        finally:
+            ecc.ecc_destroy(h2)
+        s3 = ecc.ecc_stream_begin(h, img.shape, img.dtype)
+        _push_all(h, s3, img, [10])
+        assert np.array_equal(ecc.ecc_stream_finish(h, s3), oracle.ecc_int(img, 256, "V"))
+        with pytest.raises(ecc.EccError):
+            ecc.ecc_stream_begin(h, (4, 4), np.float32)
+    finally:
+        ecc.ecc_destroy(h)
+
+
+# ---- batching ---------------------------------------------------------------
+
+def _mixed_images(n, seed, max2d=120, max3d=40):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        if rng.random() < 0.5:
+            shape = tuple(int(x) for x in rng.integers(1, max2d, size=2))
+        else:
+            shape = tuple(int(x) for x in rng.integers(1, max3d, size=3))
+        if rng.random() < 0.6:
+            out.append((synth.smooth_u8(shape, 1.0, seed + i), 256))
+        else:
+            out.append((synth.smooth_int(shape, 1.0, 16383, seed + i, np.uint16), 16384))
+    return out
+
+
+def test_batch_mixed_matches_oracle(lib):
+    import torch
+    imgs = _mixed_images(60, S + 10)
+    imgs.append((np.zeros((0, 7), np.uint8), 256))
+    imgs.append((np.full((1, 1, 1), 5, np.uint8), 256))
+    arrays = [a for a, _ in imgs]
+    bins = [b for _, b in imgs]
+    # a few as device tensors
+    for i in range(0, len(arrays), 7):
+        arrays[i] = torch.from_numpy(arrays[i]).cuda()
+    h = ecc.ecc_create(device=0)
+    try:
+        res = ecc.ecc_compute_batch(h, arrays, bins)
+    finally:
+        ecc.ecc_destroy(h)
+    for (img, b), r in zip(imgs, res):
+        assert not isinstance(r, Exception), r
+        assert np.array_equal(r, oracle.ecc_int(img, b, "V"))
+
+
+def test_batch_bad_entries_do_not_spoil_the_rest(lib):
+    good = synth.smooth_u8((20, 30, 40), 2.0, S + 11)
+    four_d = np.zeros((2, 2, 2, 2), np.uint8)
+    too_big = good.copy()
+    too_big[3, 3, 3] = 200
+    h = ecc.ecc_create(device=0)
+    try:
+        res = ecc.ecc_compute_batch(h, [good, four_d, too_big, good], [256, 256, 100, 256])
+    finally:
+        ecc.ecc_destroy(h)
+    want = oracle.ecc_int(good, 256, "V")
+    assert np.array_equal(res[0], want) and np.array_equal(res[3], want)
+    assert isinstance(res[1], ecc.EccError) and res[1].status == ecc.ECC_ERR_ARG
+    assert isinstance(res[2], ecc.EccError) and res[2].status == ecc.ECC_ERR_VALUE
+
+
+def test_batch_more_than_one_launch_worth(lib):
+    """1100 images: more than one work list (1024 images), same answers."""
+    rng = np.random.default_rng(S + 12)
+    imgs = [rng.integers(0, 256, size=(int(rng.integers(1, 9)), int(rng.integers(1, 9))),
+                         dtype=np.uint8) for _ in range(1100)]
+    h = ecc.ecc_create(device=0)
+    try:
+        res = ecc.ecc_compute_batch(h, imgs)
+    finally:
+        ecc.ecc_destroy(h)
+    for img, r in zip(imgs, res):
+        assert np.array_equal(r, oracle.ecc_int(img, 256, "V"))
+
+
+# ---- serving ----------------------------------------------------------------
+
+def test_serve_alone_equals_in_the_mix(lib):
+    imgs = _mixed_images(80, S + 20, max2d=200, max3d=48)
+    h = ecc.ecc_create(device=0, bins=16384)  # one bin count for both dtypes
+    try:
+        alone = [ecc.ecc_compute(h, img) for img, _ in imgs]
+        ids = [ecc.ecc_submit(h, img) for img, _ in imgs]
+        got = {}
+        for rid in ids:
+            st, curve = ecc.ecc_poll(h, rid, timeout_us=60_000_000)
+            assert st == ecc.ECC_OK
+            got[rid] = curve
+        lat = [ecc.ecc_request_latency_us(h, rid) for rid in ids]
+    finally:
+        ecc.ecc_destroy(h)
+    for (img, _), rid, a in zip(imgs, ids, alone):
+        assert np.array_equal(got[rid], a)
+        assert np.array_equal(a, oracle.ecc_int(img, 16384, "V"))
+    assert all(x > 0 for x in lat)
+
+
+def test_serve_memory_cap_admits_gradually(lib):
+    imgs = [synth.smooth_u8((24, 64, 64), 2.0, S + 30 + i) for i in range(12)]
+    one = 24 * 64 * 64 + 8 * (2 * 256 + 1)
+    h = ecc.ecc_create(device=0, mem_cap_bytes=3 * one)  # three requests at a time
+    try:
+        ids = [ecc.ecc_submit(h, img) for img in imgs]
+        for img, rid in zip(imgs, ids):
+            st, curve = ecc.ecc_poll(h, rid, timeout_us=60_000_000)
+            assert st == ecc.ECC_OK
+            assert np.array_equal(curve, oracle.ecc_int(img, 256, "V"))
+        with pytest.raises(ecc.EccError) as ei:
+            ecc.ecc_submit(h, np.zeros((80, 80, 80), np.uint8))  # larger than the cap
+        assert ei.value.status == ecc.ECC_ERR_OOM
+    finally:
+        ecc.ecc_destroy(h)
+
+
+def test_serve_poll_states(lib):
+    h = ecc.ecc_create(device=0)
+    try:
+        img = synth.uniform_u8((30, 30, 30), S + 40)
+        rid = ecc.ecc_submit(h, img)
+        st, _ = ecc.ecc_poll(h, rid, timeout_us=0)
+        assert st in (ecc.ECC_OK, ecc.ECC_PENDING)
+        if st == ecc.ECC_PENDING:
+            st, curve = ecc.ecc_poll(h, rid, timeout_us=60_000_000)
+            assert st == ecc.ECC_OK
+        with pytest.raises(ecc.EccError):
+            ecc.ecc_poll(h, rid, timeout_us=0)  # already retired
+        with pytest.raises(ecc.EccError):
+            ecc.ecc_poll(h, 987654321, timeout_us=0)
+        with pytest.raises(ecc.EccError) as ei:
+            ecc.ecc_submit(h, np.zeros((3, 3), np.float32))
+        assert ei.value.status == ecc.ECC_ERR_DTYPE
+    finally:
+        ecc.ecc_destroy(h)
+
+
+def test_destroy_with_requests_in_flight(lib):
+    h = ecc.ecc_create(device=0)
+    for i in range(20):
+        ecc.ecc_submit(h, synth.uniform_u8((40, 40, 40), S + 50 + i))
+    ecc.ecc_destroy(h)  # cancels cleanly

@@ -34,6 +34,8 @@ struct LocalArgs {
   int64_t w_lo = 0, w_hi = 0;   // voxel planes to process along n[0]
   int64_t w_mem_lo = 0, w_mem_hi = 0;  // planes present in memory
   int64_t bins = 256;
+  int64_t row_pitch = 0;        // bytes between rows; 0 = dense (n_x * element size).
+                                // Only the bit-sliced kernel takes a pitch.
   long long* vcec = nullptr;    // int64[bins] accumulator (integer images)
   int* err = nullptr;           // device error word
   unsigned long long* pairs = nullptr;       // float images: (key<<32 | contrib)

@@ -108,8 +108,44 @@ static int64_t max_planes_per_launch(const Shape& s, int num_sms) {
   return std::max<int64_t>(1, budget / per_plane);
 }
 
-int enqueue_int(ecc_handle* h, const void* d_img, const Shape& s, int dtype, int64_t bins,
-                long long* d_vcec, long long* d_curve, cudaStream_t stream) {
+bool bits_eligible(const ecc_handle* h, const Shape& s, int dtype, int64_t bins) {
+  return h->variant != 1 && s.view == 3 &&
+         ((dtype == kU8 && bins == 256) || (dtype == kU16 && (bins == 16384 || bins == 65536)));
+}
+
+int stage_image(ecc_handle* h, const void* image, bool on_device, const Shape& s, int dtype,
+                int64_t bins, cudaStream_t st, const void** d_img, int64_t* row_pitch) {
+  const size_t eb = dtype_bytes(dtype);
+  *row_pitch = 0;
+  *d_img = image;
+  if (s.voxels == 0) return ECC_OK;
+  const size_t dense = eb * (size_t)s.n[s.view - 1];
+  const size_t rows = (size_t)(s.voxels / s.n[s.view - 1]);
+  cudaError_t e;
+  if (bits_eligible(h, s, dtype, bins)) {
+    if (on_device && (reinterpret_cast<uintptr_t>(image) & 15u) == 0 && dense % 16 == 0)
+      return ECC_OK;
+    // rows at a 16-byte pitch so that the bit-sliced kernel can load them
+    const size_t pitch = (dense + 15) & ~size_t(15);
+    if ((e = h->img.ensure(pitch * rows))) return cuda_err(h, e, "image buffer");
+    if ((e = cudaMemcpy2DAsync(h->img.p, pitch, image, dense, dense, rows,
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                               st)))
+      return cuda_err(h, e, "copy image");
+    *d_img = h->img.p;
+    *row_pitch = (int64_t)pitch;
+    return ECC_OK;
+  }
+  if (on_device) return ECC_OK;
+  if ((e = h->img.ensure(dense * rows))) return cuda_err(h, e, "image buffer");
+  if ((e = cudaMemcpyAsync(h->img.p, image, dense * rows, cudaMemcpyHostToDevice, st)))
+    return cuda_err(h, e, "copy image");
+  *d_img = h->img.p;
+  return ECC_OK;
+}
+
+int enqueue_int(ecc_handle* h, const void* d_img, int64_t row_pitch, const Shape& s, int dtype,
+                int64_t bins, long long* d_vcec, long long* d_curve, cudaStream_t stream) {
   cudaError_t e = cudaMemsetAsync(d_vcec, 0, sizeof(long long) * bins, stream);
   if (e != cudaSuccess) return cuda_err(h, e, "memset vcec");
   if (s.voxels > 0) {
@@ -120,6 +156,7 @@ int enqueue_int(ecc_handle* h, const void* d_img, const Shape& s, int dtype, int
     a.view = s.view;
     for (int i = 0; i < 4; ++i) a.n[i] = s.n[i];
     a.bins = bins;
+    a.row_pitch = row_pitch;
     a.variant = h->variant;
     a.vcec = d_vcec;
     a.err = h->errw.as<int>();
@@ -393,14 +430,7 @@ int ecc_compute(ecc_handle* h, const void* image, const int64_t* dims, int ndim,
     if (s.voxels > 0 && !image) return set_err(h, ECC_ERR_ARG, "image is NULL");
     cudaError_t e = cudaSetDevice(h->device);
     if (e) return cuda_err(h, e, "set device");
-    const void* d_img = image;
-    if (s.voxels > 0 && !is_device_ptr(h, image)) {
-      if ((e = h->img.ensure(eb * s.voxels))) return cuda_err(h, e, "image buffer");
-      if ((e = cudaMemcpyAsync(h->img.p, image, eb * s.voxels, cudaMemcpyHostToDevice,
-                               h->stream)))
-        return cuda_err(h, e, "copy image");
-      d_img = h->img.p;
-    }
+    const bool on_dev = s.voxels > 0 && is_device_ptr(h, image);
     if ((e = cudaMemsetAsync(h->errw.p, 0, sizeof(int), h->stream)))
       return cuda_err(h, e, "memset");
     if (dtype == ECC_F32) {
@@ -410,17 +440,27 @@ int ecc_compute(ecc_handle* h, const void* image, const int64_t* dims, int ndim,
         out->chi = static_cast<int64_t*>(std::malloc(sizeof(int64_t)));
         return ECC_OK;
       }
+      const void* d_img = image;
+      if (!on_dev) {
+        if ((e = h->img.ensure(eb * s.voxels))) return cuda_err(h, e, "image buffer");
+        if ((e = cudaMemcpyAsync(h->img.p, image, eb * s.voxels, cudaMemcpyHostToDevice,
+                                 h->stream)))
+          return cuda_err(h, e, "copy image");
+        d_img = h->img.p;
+      }
       rc = compute_float(h, d_img, s, out);
       if (rc) ecc_result_free(out);
       return rc;
     }
     const int64_t bins = default_bins(h, dtype);
-    if (dtype == ECC_U8 && bins > 256 && h->cfg.bins == 0) return set_err(h, ECC_ERR_ARG, "bins");
     if ((e = h->vcec.ensure(sizeof(long long) * bins)) ||
         (e = h->curve.ensure(sizeof(long long) * bins)))
       return cuda_err(h, e, "vcec buffers");
-    rc = enqueue_int(h, d_img, s, dtype, bins, h->vcec.as<long long>(), h->curve.as<long long>(),
-                     h->stream);
+    const void* d_img = nullptr;
+    int64_t pitch = 0;
+    if ((rc = stage_image(h, image, on_dev, s, dtype, bins, h->stream, &d_img, &pitch))) return rc;
+    rc = enqueue_int(h, d_img, pitch, s, dtype, bins, h->vcec.as<long long>(),
+                     h->curve.as<long long>(), h->stream);
     if (rc) return rc;
     out->bins = bins;
     out->curve = static_cast<int64_t*>(std::malloc(sizeof(int64_t) * bins));
@@ -461,7 +501,10 @@ int ecc_compute_device(ecc_handle* h, const void* d_image, const int64_t* dims, 
     if (e) return cuda_err(h, e, "set device");
     if ((e = h->vcec.ensure(sizeof(long long) * bins))) return cuda_err(h, e, "vcec buffer");
     cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : h->stream;
-    return enqueue_int(h, d_image, s, dtype, bins, h->vcec.as<long long>(),
+    const void* d_img = nullptr;
+    int64_t pitch = 0;
+    if ((rc = stage_image(h, d_image, true, s, dtype, bins, st, &d_img, &pitch))) return rc;
+    return enqueue_int(h, d_img, pitch, s, dtype, bins, h->vcec.as<long long>(),
                        reinterpret_cast<long long*>(d_curve), st);
   } catch (...) {
     return set_err(h, ECC_ERR_CUDA, "internal error");

@@ -90,8 +90,15 @@ size_t dtype_bytes(int dtype);
 bool is_device_ptr(const ecc_handle* h, const void* p);
 // Enqueues VCEC accumulation (zeroed first) + contribution kernel + scan of
 // an integer image already on the device.
-int enqueue_int(ecc_handle* h, const void* d_img, const Shape& s, int dtype, int64_t bins,
-                long long* d_vcec, long long* d_curve, cudaStream_t stream);
+int enqueue_int(ecc_handle* h, const void* d_img, int64_t row_pitch, const Shape& s, int dtype,
+                int64_t bins, long long* d_vcec, long long* d_curve, cudaStream_t stream);
+// True when the bit-sliced kernel applies to this shape / dtype / bin count.
+bool bits_eligible(const ecc_handle* h, const Shape& s, int dtype, int64_t bins);
+// Device copy of an image for the contribution kernels: in place if possible,
+// else into the handle's image buffer (rows at a 16-byte pitch when the
+// bit-sliced kernel applies). *row_pitch = 0 means dense rows.
+int stage_image(ecc_handle* h, const void* image, bool on_device, const Shape& s, int dtype,
+                int64_t bins, cudaStream_t st, const void** d_img, int64_t* row_pitch);
 // Bounded wait on an event (host side); ECC_ERR_TIMEOUT after timeout_us.
 int wait_event(ecc_handle* h, cudaEvent_t ev, int64_t timeout_us);
 cudaError_t launch_local(const LocalArgs& a, int num_sms, int64_t* launches);

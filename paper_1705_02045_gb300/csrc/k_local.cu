@@ -230,6 +230,8 @@ cudaError_t launch_conv(const LocalArgs& a, int num_sms, int64_t* launches) {
 }  // namespace
 
 cudaError_t launch_local_generic(const LocalArgs& a, int num_sms, int64_t* launches) {
+  const int64_t eb = a.dtype == kU8 ? 1 : a.dtype == kU16 ? 2 : 4;
+  if (a.row_pitch > 0 && a.row_pitch != a.n[a.view - 1] * eb) return cudaErrorInvalidValue;
   switch (a.dtype) {
     case kU8: return launch_conv<uint8_t>(a, num_sms, launches);
     case kU16: return launch_conv<uint16_t>(a, num_sms, launches);

@@ -34,7 +34,10 @@ struct ecc_stream {
   Shape s;          // kernel view: marching axis n[0] = dims[0]
   int dtype = kU8;
   int64_t bins = 256;
-  size_t plane_bytes = 0;
+  size_t plane_bytes = 0;   // bytes of one plane in a ring slot
+  size_t src_row = 0;       // bytes of one dense row in the caller's planes
+  size_t rows_per_plane = 0;
+  int64_t row_pitch = 0;    // slot row pitch (0 = dense)
   int64_t depth = 64;
   int R = 0;
   DevBuf ring, vcec, curve;
@@ -67,6 +70,7 @@ int launch_slot(ecc_stream* st, int k, bool has_upper) {
   a.w_mem_lo = sl.z0 - 1;
   a.w_mem_hi = sl.z0 + sl.nz + (has_upper ? 1 : 0);
   a.bins = st->bins;
+  a.row_pitch = st->row_pitch;
   a.variant = h->variant;
   a.vcec = st->vcec.as<long long>();
   a.err = h->errw.as<int>();
@@ -130,7 +134,15 @@ int ecc_stream_begin(ecc_handle* h, const int64_t* dims, int ndim, ecc_dtype dty
     st->s = s;
     st->dtype = dtype;
     st->bins = default_bins(h, dtype);
-    st->plane_bytes = dtype_bytes(dtype) * (size_t)(s.voxels / std::max<int64_t>(dims[0], 1));
+    // rows of the slots at a 16-byte pitch when the bit-sliced kernel applies
+    st->src_row = dtype_bytes(dtype) * (size_t)s.n[s.view - 1];
+    st->rows_per_plane = s.voxels > 0 ? (size_t)(s.voxels / s.n[0] / s.n[s.view - 1]) : 0;
+    size_t slot_row = st->src_row;
+    if (bits_eligible(h, s, dtype, st->bins) && st->src_row % 16 != 0) {
+      slot_row = (st->src_row + 15) & ~size_t(15);
+      st->row_pitch = (int64_t)slot_row;
+    }
+    st->plane_bytes = slot_row * st->rows_per_plane;
     if (s.voxels == 0) st->plane_bytes = 0;
     st->depth = std::max<int64_t>(1, h->cfg.slab_depth);
     if (st->plane_bytes > 0) {
@@ -199,8 +211,15 @@ int ecc_stream_push_slab(ecc_stream* st, const void* host_planes, int64_t z0, in
       StreamSlot& sl = st->slots[k];
       char* base = slot_base(st, k);
       if (sl.used && (e = cudaStreamWaitEvent(h->copy_stream, sl.freed, 0))) break;
-      if ((e = cudaMemcpyAsync(base + st->plane_bytes, src + off * st->plane_bytes,
-                               cnz * st->plane_bytes, cudaMemcpyHostToDevice, h->copy_stream)) ||
+      const size_t src_plane = st->src_row * st->rows_per_plane;
+      if (st->row_pitch)
+        e = cudaMemcpy2DAsync(base + st->plane_bytes, (size_t)st->row_pitch, src + off * src_plane,
+                              st->src_row, st->src_row, cnz * st->rows_per_plane,
+                              cudaMemcpyHostToDevice, h->copy_stream);
+      else
+        e = cudaMemcpyAsync(base + st->plane_bytes, src + off * src_plane, cnz * src_plane,
+                            cudaMemcpyHostToDevice, h->copy_stream);
+      if (e ||
           (e = cudaEventRecord(sl.copied, h->copy_stream)) ||
           (e = cudaStreamWaitEvent(h->stream, sl.copied, 0)))
         break;

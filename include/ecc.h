@@ -201,6 +201,35 @@ int64_t ecc_launch_count(const ecc_handle* h);
 int ecc_set_profiling(ecc_handle* h, int on);
 int ecc_profile_read(ecc_handle* h, double* contrib_ms, int64_t* count);
 
+/* ECC of an integer image already on the device, for callers that cannot
+ * allocate device memory: for example a host program that has handed all of
+ * the GPU's memory to its own pool allocator and may not let a library
+ * allocate beside it, or one that must stay inside a fixed, pre-planned
+ * memory budget. It needs no handle and allocates nothing. The paper has no
+ * counterpart of this entry point.
+ *
+ * What the computation needs besides the caller's image and curve (the int64
+ * change vector and an error word) sits in file-scope device arrays of this
+ * library: 65536 int64 counters (512 KiB) plus 256 bytes, held by every GPU
+ * that loads the library until the process exits. Hence bins must lie in
+ * 1..65536; a larger bins returns ECC_ERR_ARG.
+ *
+ * d_image: device image of the current device, layout as everywhere in this
+ * header (ECC_U8 or ECC_U16, 1 <= ndim <= 4). convention: ECC_CONV_V or
+ * ECC_CONV_T. d_curve: device int64[bins], written with chi(K_t). stream: a
+ * cudaStream_t (NULL = the legacy default stream); the call enqueues its work
+ * there and waits for it before returning. Errors: ECC_ERR_ARG, ECC_ERR_DTYPE,
+ * ECC_ERR_VALUE (a value >= bins), ECC_ERR_CUDA.
+ *
+ * The first call on a device (with that device current) looks up the
+ * arrays' device address; make that first call before any stream capture.
+ * All calls on a device share the arrays, and each call clears them first:
+ * calls that overlap on the GPU (from several host threads or streams) race
+ * and give wrong results. */
+int ecc_compute_device_noalloc(const void* d_image, const int64_t* dims, int ndim,
+                               ecc_dtype dtype, int64_t bins, int convention,
+                               int64_t* d_curve, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

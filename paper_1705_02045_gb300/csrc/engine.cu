@@ -101,7 +101,7 @@ cudaError_t launch_local(const LocalArgs& a, int num_sms, int64_t* launches) {
 // block's int32 shared-memory histogram can overflow: a change is at most 21
 // in magnitude (|G_4| <= 3 * 7), and a launch splits its voxels over at least
 // `blocks` blocks of which none takes more than twice its share.
-static int64_t max_planes_per_launch(const Shape& s, int num_sms) {
+int64_t max_planes_per_launch(const Shape& s, int num_sms) {
   const int64_t per_plane = s.voxels / std::max<int64_t>(s.n[0], 1);
   const int64_t budget = (int64_t(1) << 31) / 32 * (int64_t)num_sms / 2;
   if (per_plane <= 0) return s.n[0];

@@ -102,6 +102,9 @@ int stage_image(ecc_handle* h, const void* image, bool on_device, const Shape& s
 // Bounded wait on an event (host side); ECC_ERR_TIMEOUT after timeout_us.
 int wait_event(ecc_handle* h, cudaEvent_t ev, int64_t timeout_us);
 cudaError_t launch_local(const LocalArgs& a, int num_sms, int64_t* launches);
+// Planes of n[0] per contribution launch that keep every block's int32
+// shared-memory histogram from overflowing.
+int64_t max_planes_per_launch(const Shape& s, int num_sms);
 void serve_shutdown(ecc_handle* h);
 
 }  // namespace ecc

@@ -70,6 +70,8 @@ _SIGNATURES = {
     "ecc_launch_count": (C.c_int64, [_P]),
     "ecc_set_profiling": (C.c_int, [_P, C.c_int]),
     "ecc_profile_read": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "ecc_compute_device_noalloc": (C.c_int, [_P, _I64P, C.c_int, C.c_int, C.c_int64, C.c_int,
+                                             _P, _P]),
 }
 
 _lib = None
@@ -302,3 +304,14 @@ def ecc_profile_read(h):
     ms, n = C.c_double(), C.c_int64()
     _check(h, load().ecc_profile_read(h, C.byref(ms), C.byref(n)))
     return ms.value, n.value
+
+
+def ecc_compute_device_noalloc(d_image, bins: int, d_curve, convention: int = ECC_CONV_V,
+                               stream=None) -> int:
+    """Status of the allocation-free integer entry point on CUDA tensors
+    (``d_curve``: int64 CUDA tensor of ``bins`` entries)."""
+    st = C.c_void_p(stream.cuda_stream) if stream is not None else None
+    return int(load().ecc_compute_device_noalloc(
+        C.c_void_p(d_image.data_ptr()), _dims(d_image.shape), len(d_image.shape),
+        _dtype_code(d_image.dtype), int(bins), int(convention),
+        C.c_void_p(d_curve.data_ptr()), st))

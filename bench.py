@@ -149,6 +149,110 @@ def cpu_baseline(img, seconds: float = 15.0):
                       "(numpy, single thread)"}
 
 
+def make_requests(n: int, seed: int):
+    """The mixed request stream (shapes/dtypes of synth.request_mix, smoothed
+    fields sigma = 2 requantised to each dtype's range), generated on the GPU
+    and returned as host numpy arrays with their bin counts."""
+    from paper_1705_02045_gb300 import synth
+    out = []
+    for i, (shape, dt, bins) in enumerate(synth.request_mix(n, seed)):
+        t = synth.smooth_int_torch(shape, 2.0, bins - 1, seed + 1 + i)
+        out.append((t.cpu().numpy().astype(dt), bins))
+    return out
+
+
+def bench_batched(h, reqs, stream):
+    """One launch sequence per image vs one batched launch, same device images.
+    Both include copying every curve back to the host."""
+    import torch
+    from paper_1705_02045_gb300 import ecc
+    dev = [torch.from_numpy(a).cuda() for a, _ in reqs]
+    bins = [b for _, b in reqs]
+    curves = [torch.empty(b, dtype=torch.int64, device="cuda") for b in bins]
+    vox = sum(a.size for a, _ in reqs)
+
+    def per_image():
+        for d, b, c in zip(dev, bins, curves):
+            ecc.ecc_compute_device(h, d, b, c, stream=stream)
+        stream.synchronize()
+        return [c.cpu() for c in curves]
+
+    def batched():
+        return ecc.ecc_compute_batch(h, dev, bins)
+
+    per_image()
+    batched()
+    torch.cuda.synchronize()
+    t_per, t_bat = [], []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        ref = per_image()
+        t_per.append(time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        res = batched()
+        t_bat.append(time.perf_counter() - t0)
+    same = all(np.array_equal(r.numpy(), b) for r, b in zip(ref, res))
+    assert same, "batched curves differ from per-image curves"
+    tp, tb = min(t_per), min(t_bat)
+    return {"images": len(reqs), "voxels": int(vox), "per_image_s": tp, "batched_s": tb,
+            "speedup": tp / tb, "gvox_s_batched": vox / tb / 1e9,
+            "gvox_s_per_image": vox / tp / 1e9, "identical": bool(same)}
+
+
+def bench_serving(h, reqs, rate_hz: float, seed: int):
+    """Requests submitted at Poisson arrival times (rate_hz), polled to
+    completion; latency = submit -> completion as recorded by the library.
+    rate_hz = 0: all submitted at once (saturated)."""
+    from paper_1705_02045_gb300 import ecc
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate_hz, size=len(reqs)) if rate_hz > 0 else np.zeros(len(reqs))
+    arrivals = np.cumsum(gaps)
+    ids = [None] * len(reqs)
+
+    def submitter():
+        t0 = time.perf_counter()
+        for i, (img, _) in enumerate(reqs):
+            dt = arrivals[i] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            ids[i] = ecc.ecc_submit(h, img)
+
+    t0 = time.perf_counter()
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    for rid in ids:
+        st, _ = ecc.ecc_poll(h, rid, timeout_us=600_000_000)
+        assert st == ecc.ECC_OK
+    wall = time.perf_counter() - t0
+    lat = np.array([ecc.ecc_request_latency_us(h, rid) for rid in ids]) / 1e3
+    vox = sum(a.size for a, _ in reqs)
+    return {"requests": len(reqs), "rate_hz": rate_hz, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "gvox_s": vox / wall / 1e9, "wall_s": wall}
+
+
+def profile_case(args):
+    """A few launches of the integer path on one image, nothing else: the
+    small, self-ending case for ncu captures."""
+    import torch
+    from paper_1705_02045_gb300 import ecc, synth
+    shape = tuple(int(s) for s in args.profile_shape.split(","))
+    if args.profile_dtype == "u8":
+        img, bins = synth.smooth_u8(shape, SIGMA, synth.SEED_BASE + 1), 256
+    else:
+        img, bins = synth.two_phase_u16(shape, 6.0, synth.SEED_BASE + 2), 16384
+    h = ecc.ecc_create(device=0)
+    d = torch.from_numpy(img).cuda()
+    c = torch.empty(bins, dtype=torch.int64, device="cuda")
+    for _ in range(args.profile_launches):
+        ecc.ecc_compute_device(h, d, bins, c)
+    torch.cuda.synchronize()
+    assert ecc.ecc_device_status(h) == ecc.ECC_OK and int(c[-1]) == 1
+    ecc.ecc_destroy(h)
+    print("profile case ok", shape, args.profile_dtype)
+
+
 def run_reference(args, world, rank):
     """--impl reference: the CPU oracle, timed on this host, rank 0 only."""
     if rank != 0:
@@ -194,8 +298,19 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--batch-images", type=int, default=512,
+                    help="images of the mixed request stream in the batched comparison")
+    ap.add_argument("--serve-requests", type=int, default=1024,
+                    help="requests of the served Poisson stream (0 = skip)")
+    ap.add_argument("--profile-launches", type=int, default=0,
+                    help="only run this many ecc_compute_device launches (for ncu) and exit")
+    ap.add_argument("--profile-shape", default="640,512,512")
+    ap.add_argument("--profile-dtype", default="u8", choices=["u8", "u16"])
     args = ap.parse_args()
     world, rank, local = _dist()
+    if args.profile_launches > 0:
+        profile_case(args)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
         return
@@ -301,6 +416,32 @@ def main():
             "gpu_launches": int(launches),
             "clocks": cs,
         }
+        if args.batch_images > 0 or args.serve_requests > 0:
+            from paper_1705_02045_gb300 import synth
+            n_req = max(args.batch_images, args.serve_requests)
+            reqs = make_requests(n_req, synth.SEED_BASE + 3)
+            hb = ecc.ecc_create(device=local)
+            try:
+                if args.batch_images > 0:
+                    line["batched"] = bench_batched(hb, reqs[:args.batch_images], stream)
+            finally:
+                ecc.ecc_destroy(hb)
+            if args.serve_requests > 0:
+                sreqs = reqs[:args.serve_requests]
+                hs = ecc.ecc_create(device=local)
+                try:
+                    sat = bench_serving(hs, sreqs, 0.0, synth.SEED_BASE + 4)
+                finally:
+                    ecc.ecc_destroy(hs)
+                rate = 0.8 * len(sreqs) / sat["wall_s"]
+                hs = ecc.ecc_create(device=local)
+                try:
+                    pois = bench_serving(hs, sreqs, rate, synth.SEED_BASE + 5)
+                finally:
+                    ecc.ecc_destroy(hs)
+                line["serving"] = {"poisson_0.8x": pois, "saturated": sat,
+                                   "workload": "mixed 2D/3D uint8 / 14-bit uint16 requests, "
+                                               "smoothed fields sigma=2 (synth.request_mix)"}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(img)
         print(json.dumps(line), flush=True)

@@ -6,16 +6,19 @@
 // (image, tile range) items, balanced by voxel work on the host, is walked by
 // a fixed grid; each block keeps a private shared-memory histogram per image
 // (flushed when the image changes) and every image has its own int64 VCEC.
-// The launch sequence (zero VCECs, batched contribution kernel, batched scan)
-// is captured once per slot in a CUDA graph whose kernels read the batch from
-// a fixed device descriptor buffer; a new batch only re-uploads the
-// descriptors and replays the graph.
+// Images the bit-sliced kernel takes (1-3D, uint8 with 256 bins or uint16 with
+// 16384 / 65536 bins) go to the batched bit-sliced kernel, the others to the
+// batched generic kernel. The launch sequence (zero VCECs, the two batched
+// contribution kernels, batched scan) is captured once per slot in a CUDA
+// graph whose kernels read the batch from a fixed device descriptor buffer; a
+// new batch only re-uploads the descriptors and replays the graph.
 //
 // Serving (ecc_submit / ecc_poll): a scheduler thread admits requests while
 // their device memory fits under the cap, launches the admitted ones as a
 // batch on one of two slots (two streams), and keeps launching new batches
 // while earlier ones run (continuous batching). Completion is detected by
 // events; results move to the request, device memory returns to the cap.
+#include "ecc_bits.cuh"
 #include "ecc_scan.cuh"
 #include "ecc_tile.cuh"
 #include "engine.h"
@@ -26,6 +29,8 @@
 
 namespace ecc {
 
+int bits_nb(int dtype, int64_t bins);  // k_bits.cu
+
 struct BImage {
   const void* img;
   long long* vcec;
@@ -33,9 +38,11 @@ struct BImage {
   int* err;
   int64_t n[3];  // z, y, x
   int64_t bins;
-  int64_t tiles_x, tiles_y, zc;
+  int64_t row_pitch;  // bytes (bit-sliced images)
+  int64_t tiles_x, tiles_y, zc;  // generic tiling
+  BitsGeo geo;        // bit-sliced tiling
   int dtype;
-  int smem_hist;
+  int nb;             // 0: generic kernel; 8 / 14 / 16: bit-sliced kernel
 };
 
 struct BItem {
@@ -46,32 +53,40 @@ struct BItem {
 
 struct BHeader {
   int n_images;
-  int n_items;
+  int n_items_bits, n_items_gen;
 };
 
 constexpr int kMaxBatch = 1024;
 constexpr int64_t kSmallBins = 256;
+constexpr int kBatchBitsWarps = 8;
+constexpr int kBatchPlRec = 17;  // odd and >= 16 + 1 planes
 
 namespace {
 
 struct DescLayout {
-  size_t hdr = 0, imgs = 0, items = 0, starts = 0, total = 0;
-  int item_cap = 0;
+  size_t hdr = 0, imgs = 0, items_b = 0, starts_b = 0, items_g = 0, starts_g = 0, total = 0;
+  int item_cap_b = 0, item_cap_g = 0, grid_b = 0, grid_g = 0;
 };
 
-DescLayout desc_layout(int grid) {
+DescLayout desc_layout(int grid_b, int grid_g) {
   auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
   DescLayout L;
-  L.item_cap = kMaxBatch + grid + 1;
+  L.grid_b = grid_b;
+  L.grid_g = grid_g;
+  L.item_cap_b = kMaxBatch + grid_b + 1;
+  L.item_cap_g = kMaxBatch + grid_g + 1;
   size_t o = 0;
   L.hdr = o; o += up(sizeof(BHeader));
   L.imgs = o; o += up(sizeof(BImage) * kMaxBatch);
-  L.items = o; o += up(sizeof(BItem) * L.item_cap);
-  L.starts = o; o += up(sizeof(int) * (grid + 1));
+  L.items_b = o; o += up(sizeof(BItem) * L.item_cap_b);
+  L.starts_b = o; o += up(sizeof(int) * (grid_b + 1));
+  L.items_g = o; o += up(sizeof(BItem) * L.item_cap_g);
+  L.starts_g = o; o += up(sizeof(int) * (grid_g + 1));
   L.total = o;
   return L;
 }
 
+// ---- batched generic kernel (images the bit-sliced kernel does not take) ----
 template <int CONV, int SMEM_BINS>
 __global__ void __launch_bounds__(kTileThreads)
 k_batch3(const unsigned char* __restrict__ desc, DescLayout L) {
@@ -80,12 +95,13 @@ k_batch3(const unsigned char* __restrict__ desc, DescLayout L) {
   int8_t* g2 = reinterpret_cast<int8_t*>(ring + 4 * kT3PL);
   int* hist = reinterpret_cast<int*>(g2 + 256);
   const BImage* imgs = reinterpret_cast<const BImage*>(desc + L.imgs);
-  const BItem* items = reinterpret_cast<const BItem*>(desc + L.items);
-  const int* starts = reinterpret_cast<const int*>(desc + L.starts);
+  const BItem* items = reinterpret_cast<const BItem*>(desc + L.items_g);
+  const int* starts = reinterpret_cast<const int*>(desc + L.starts_g);
+  const int i0 = starts[blockIdx.x], i1 = starts[blockIdx.x + 1];
+  if (i0 >= i1) return;
   g2[threadIdx.x] = (int8_t)g2_entry(threadIdx.x);
   for (int b = threadIdx.x; b < SMEM_BINS; b += kTileThreads) hist[b] = 0;
   __syncthreads();
-  const int i0 = starts[blockIdx.x], i1 = starts[blockIdx.x + 1];
   for (int it = i0; it < i1; ++it) {
     const BItem item = items[it];
     const BImage& im = imgs[item.image];
@@ -94,7 +110,7 @@ k_batch3(const unsigned char* __restrict__ desc, DescLayout L) {
     s.vcec = im.vcec;
     s.hist = hist;
     s.err = im.err;
-    const bool smem_hist = im.smem_hist && im.bins <= SMEM_BINS;
+    const bool smem_hist = im.bins <= SMEM_BINS;
     const int64_t txy = im.tiles_x * im.tiles_y;
     for (int64_t t = item.tile_lo; t < item.tile_hi; ++t) {
       const int64_t tz = t / txy, rem = t - tz * txy;
@@ -122,6 +138,69 @@ k_batch3(const unsigned char* __restrict__ desc, DescLayout L) {
   }
 }
 
+// ---- batched bit-sliced kernel ----------------------------------------------
+template <int CONV, int NB, int HM>
+__device__ void bits_item(const BImage& im, const BItem& item, uint32_t* pl, uint32_t* g0,
+                          uint32_t* g1, int* hist) {
+  BitsImg bi;
+  bi.img = static_cast<const unsigned char*>(im.img);
+  bi.n[0] = im.n[0];
+  bi.n[1] = im.n[1];
+  bi.n[2] = im.n[2];
+  bi.row_pitch = im.row_pitch;
+  bi.w_lo = 0;
+  bi.w_hi = im.n[0];
+  bi.w_mem_lo = 0;
+  bi.w_mem_hi = im.n[0];
+  bi.bins = im.bins;
+  bi.vcec = im.vcec;
+  bi.err = im.err;
+  for (int64_t t = item.tile_lo; t < item.tile_hi; ++t)
+    bits_tile<NB, CONV, HM>(bi, im.geo, t, pl, g0, g1, kBatchPlRec, hist);
+}
+
+template <int CONV, int SMEM_BINS>
+__global__ void __launch_bounds__(32 * kBatchBitsWarps, 2)
+k_batch_bits(const unsigned char* __restrict__ desc, DescLayout L) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  const int recs = 32 * kBatchBitsWarps;
+  uint32_t* pl = sm;
+  uint32_t* g0 = pl + recs * kBatchPlRec;
+  uint32_t* g1 = g0 + recs * kBitsG0Rec;
+  int* hist = reinterpret_cast<int*>(g1 + 2 * recs * kBitsG1Rec);
+  const BImage* imgs = reinterpret_cast<const BImage*>(desc + L.imgs);
+  const BItem* items = reinterpret_cast<const BItem*>(desc + L.items_b);
+  const int* starts = reinterpret_cast<const int*>(desc + L.starts_b);
+  const int i0 = starts[blockIdx.x], i1 = starts[blockIdx.x + 1];
+  if (i0 >= i1) return;
+  for (int b = threadIdx.x; b < SMEM_BINS; b += blockDim.x) hist[b] = 0;
+  __syncthreads();
+  for (int it = i0; it < i1; ++it) {
+    const BItem item = items[it];
+    const BImage& im = imgs[item.image];
+    const bool smem_hist = im.bins <= SMEM_BINS;
+    if (smem_hist) {
+      if (im.nb == 8) bits_item<CONV, 8, kBitsSmem>(im, item, pl, g0, g1, hist);
+      else if (im.nb == 14) bits_item<CONV, 14, kBitsSmem>(im, item, pl, g0, g1, hist);
+      else bits_item<CONV, 16, kBitsSmem>(im, item, pl, g0, g1, hist);
+      __syncthreads();
+      for (int64_t b = threadIdx.x; b < im.bins; b += blockDim.x) {
+        const int v = hist[b];
+        if (v) {
+          atomicAdd(reinterpret_cast<unsigned long long*>(im.vcec) + b,
+                    (unsigned long long)(long long)v);
+          hist[b] = 0;
+        }
+      }
+      __syncthreads();
+    } else {
+      if (im.nb == 8) bits_item<CONV, 8, kBitsGlobal>(im, item, pl, g0, g1, hist);
+      else if (im.nb == 14) bits_item<CONV, 14, kBitsGlobal>(im, item, pl, g0, g1, hist);
+      else bits_item<CONV, 16, kBitsGlobal>(im, item, pl, g0, g1, hist);
+    }
+  }
+}
+
 __global__ void k_batch_zero(const unsigned char* __restrict__ desc, DescLayout L) {
   const BHeader* hdr = reinterpret_cast<const BHeader*>(desc + L.hdr);
   if ((int)blockIdx.x >= hdr->n_images) return;
@@ -138,9 +217,13 @@ k_batch_scan(const unsigned char* __restrict__ desc, DescLayout L) {
   block_scan_curve(im.vcec, im.curve, im.bins);
 }
 
-template <int CONV, int SMEM_BINS>
-size_t batch_smem() {
-  return 4 * kT3PL * 4 + 256 + sizeof(int) * SMEM_BINS;
+template <int SMEM_BINS>
+size_t gen_smem() { return 4 * kT3PL * 4 + 256 + sizeof(int) * SMEM_BINS; }
+
+template <int SMEM_BINS>
+size_t bits_smem() {
+  const size_t recs = 32 * kBatchBitsWarps;
+  return recs * (kBatchPlRec + kBitsG0Rec + 2 * kBitsG1Rec) * 4 + sizeof(int) * SMEM_BINS;
 }
 
 }  // namespace
@@ -149,13 +232,13 @@ size_t batch_smem() {
 // captured graphs (small histograms <= 256 bins, large <= 16384 bins).
 struct Slot {
   cudaStream_t stream = nullptr;
-  int grid_small = 0, grid_large = 0, grid = 0;
   DescLayout L;
   DevBuf desc;
   unsigned char* h_desc = nullptr;
   DevBuf arena;
   unsigned char* h_arena = nullptr;
   size_t h_arena_cap = 0;
+  DevBuf staging;  // pitched copies of host / unaligned images
   cudaGraphExec_t exec_small = nullptr, exec_large = nullptr;
   cudaEvent_t done = nullptr;
 };
@@ -171,21 +254,28 @@ struct ImgSpec {
   int64_t n[3];
   int dtype;
   int64_t bins;
+  int64_t row_pitch;  // bytes between rows of d_img (0 = dense)
 };
 
 template <int CONV>
 cudaError_t capture_graph(Slot& sl, bool large, cudaGraphExec_t* out) {
   cudaError_t e;
   cudaGraph_t g = nullptr;
+  const unsigned char* d = sl.desc.as<unsigned char>();
   if ((e = cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal))) return e;
-  k_batch_zero<<<kMaxBatch, 256, 0, sl.stream>>>(sl.desc.as<unsigned char>(), sl.L);
-  if (large)
-    k_batch3<CONV, kSmemBinsMax><<<sl.grid, kTileThreads, batch_smem<CONV, kSmemBinsMax>(),
-                                   sl.stream>>>(sl.desc.as<unsigned char>(), sl.L);
-  else
-    k_batch3<CONV, kSmallBins><<<sl.grid, kTileThreads, batch_smem<CONV, kSmallBins>(),
-                                 sl.stream>>>(sl.desc.as<unsigned char>(), sl.L);
-  k_batch_scan<<<kMaxBatch, kScanThreads, 0, sl.stream>>>(sl.desc.as<unsigned char>(), sl.L);
+  k_batch_zero<<<kMaxBatch, 256, 0, sl.stream>>>(d, sl.L);
+  if (large) {
+    k_batch_bits<CONV, kSmemBinsMax><<<sl.L.grid_b, 32 * kBatchBitsWarps,
+                                       bits_smem<kSmemBinsMax>(), sl.stream>>>(d, sl.L);
+    k_batch3<CONV, kSmemBinsMax><<<sl.L.grid_g, kTileThreads, gen_smem<kSmemBinsMax>(),
+                                   sl.stream>>>(d, sl.L);
+  } else {
+    k_batch_bits<CONV, kSmallBins><<<sl.L.grid_b, 32 * kBatchBitsWarps, bits_smem<kSmallBins>(),
+                                     sl.stream>>>(d, sl.L);
+    k_batch3<CONV, kSmallBins><<<sl.L.grid_g, kTileThreads, gen_smem<kSmallBins>(),
+                                 sl.stream>>>(d, sl.L);
+  }
+  k_batch_scan<<<kMaxBatch, kScanThreads, 0, sl.stream>>>(d, sl.L);
   e = cudaStreamEndCapture(sl.stream, &g);
   if (e) return e;
   e = cudaGraphInstantiate(out, g, 0);
@@ -193,38 +283,45 @@ cudaError_t capture_graph(Slot& sl, bool large, cudaGraphExec_t* out) {
   return e;
 }
 
+// Resident blocks of each batched contribution kernel (the large-histogram
+// variants, which fit the fewest blocks, fix the persistent grid sizes).
 template <int CONV>
-cudaError_t grid_for(int num_sms, int* g_small, int* g_large) {
+cudaError_t grids_for(int num_sms, int* grid_b, int* grid_g) {
   cudaError_t e;
-  auto ks = k_batch3<CONV, kSmallBins>;
-  auto kl = k_batch3<CONV, kSmemBinsMax>;
-  const size_t ss = batch_smem<CONV, kSmallBins>(), sl = batch_smem<CONV, kSmemBinsMax>();
-  if ((e = cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss)) ||
-      (e = cudaFuncSetAttribute(kl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl)))
+  auto kbs = k_batch_bits<CONV, kSmallBins>;
+  auto kbl = k_batch_bits<CONV, kSmemBinsMax>;
+  auto kgs = k_batch3<CONV, kSmallBins>;
+  auto kgl = k_batch3<CONV, kSmemBinsMax>;
+  if ((e = cudaFuncSetAttribute(kbs, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)bits_smem<kSmallBins>())) ||
+      (e = cudaFuncSetAttribute(kbl, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)bits_smem<kSmemBinsMax>())) ||
+      (e = cudaFuncSetAttribute(kgs, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)gen_smem<kSmallBins>())) ||
+      (e = cudaFuncSetAttribute(kgl, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)gen_smem<kSmemBinsMax>())))
     return e;
-  int ps = 0, pl = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, ks, kTileThreads, ss)) ||
-      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pl, kl, kTileThreads, sl)))
+  int pb = 0, pg = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pb, kbl, 32 * kBatchBitsWarps,
+                                                         bits_smem<kSmemBinsMax>())) ||
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pg, kgl, kTileThreads,
+                                                         gen_smem<kSmemBinsMax>())))
     return e;
-  *g_small = std::max(ps, 1) * num_sms;
-  *g_large = std::max(pl, 1) * num_sms;
+  *grid_b = std::max(pb, 1) * num_sms;
+  *grid_g = std::max(pg, 1) * num_sms;
   return cudaSuccess;
 }
 
 int slot_init(ecc_handle* h, Slot& sl) {
   cudaError_t e;
-  int gs = 0, gl = 0;
-  e = h->cfg.convention == kConvT ? grid_for<kConvT>(h->num_sms, &gs, &gl)
-                                  : grid_for<kConvV>(h->num_sms, &gs, &gl);
+  int gb = 0, gg = 0;
+  e = h->cfg.convention == kConvT ? grids_for<kConvT>(h->num_sms, &gb, &gg)
+                                  : grids_for<kConvV>(h->num_sms, &gb, &gg);
   if (e) return cuda_err(h, e, "batch occupancy");
-  sl.grid_small = gs;
-  sl.grid_large = gl;
-  sl.grid = std::max(gs, gl);  // one descriptor layout fits both graphs
-  sl.L = desc_layout(sl.grid);
+  sl.L = desc_layout(gb, gg);
   if ((e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking)) ||
       (e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming)) ||
-      (e = sl.desc.ensure(sl.L.total)) ||
-      (e = cudaMallocHost(&sl.h_desc, sl.L.total)))
+      (e = sl.desc.ensure(sl.L.total)) || (e = cudaMallocHost(&sl.h_desc, sl.L.total)))
     return cuda_err(h, e, "batch slot");
   std::memset(sl.h_desc, 0, sl.L.total);
   return ECC_OK;
@@ -238,6 +335,7 @@ void slot_free(Slot& sl) {
   if (sl.h_arena) cudaFreeHost(sl.h_arena);
   sl.desc.release();
   sl.arena.release();
+  sl.staging.release();
   if (sl.done) cudaEventDestroy(sl.done);
   if (sl.stream) cudaStreamDestroy(sl.stream);
   sl = Slot();
@@ -246,11 +344,49 @@ void slot_free(Slot& sl) {
 // Per-image arena record: vcec[bins], curve[bins], err word.
 size_t arena_bytes(int64_t bins) { return sizeof(long long) * (2 * bins + 1); }
 
-// Fills the slot's host descriptors for `specs` and uploads them; launches the
-// captured graph; copies curves and error words to the slot's pinned arena.
-// Returns the ECC status; on success *large tells which graph ran.
-int slot_run(ecc_handle* h, Slot& sl, const std::vector<ImgSpec>& specs, cudaStream_t wait_on,
-             cudaEvent_t wait_ev) {
+// Bit-sliced kernel for this image? (needs 16-byte aligned rows)
+int image_nb(const ecc_handle* h, const ImgSpec& sp) {
+  if (h->variant == 1) return 0;
+  const int nb = bits_nb(sp.dtype, sp.bins);
+  if (!nb) return 0;
+  const int64_t eb = sp.dtype == kU8 ? 1 : 2;
+  const int64_t pitch = sp.row_pitch > 0 ? sp.row_pitch : sp.n[2] * eb;
+  if ((reinterpret_cast<uintptr_t>(sp.d_img) & 15u) != 0 || (pitch & 15) != 0) return 0;
+  return nb;
+}
+
+// Splits tiles[i] tiles of cost cost[i] (images in order) into per-block
+// contiguous item ranges of about equal work.
+int partition(const std::vector<int>& img_of, const std::vector<int64_t>& tiles,
+              const std::vector<int64_t>& cost, int grid, BItem* items, int item_cap,
+              int* starts) {
+  double total = 0;
+  for (size_t j = 0; j < tiles.size(); ++j) total += (double)tiles[j] * cost[j];
+  const double per_block = total / grid;
+  int n_items = 0, b = 0;
+  double acc = 0;
+  starts[0] = 0;
+  for (size_t j = 0; j < tiles.size(); ++j) {
+    int64_t t = 0;
+    while (t < tiles[j]) {
+      const double room = per_block * (b + 1) - acc;
+      int64_t k = std::max<int64_t>(1, (int64_t)(room / cost[j] + 0.999));
+      k = std::min(k, tiles[j] - t);
+      if (n_items >= item_cap) return -1;
+      items[n_items++] = BItem{img_of[j], 0, t, t + k};
+      t += k;
+      acc += (double)k * cost[j];
+      while (b < grid - 1 && acc >= per_block * (b + 1) - 1e-9) starts[++b] = n_items;
+    }
+  }
+  while (b < grid) starts[++b] = n_items;
+  return n_items;
+}
+
+// Fills the slot's host descriptors for `specs`, uploads them, replays the
+// captured graph and copies curves and error words to the slot's pinned
+// arena; the slot's `done` event marks completion.
+int slot_run(ecc_handle* h, Slot& sl, const std::vector<ImgSpec>& specs, cudaEvent_t wait_ev) {
   cudaError_t e;
   const int n = (int)specs.size();
   bool large = false;
@@ -269,63 +405,59 @@ int slot_run(ecc_handle* h, Slot& sl, const std::vector<ImgSpec>& specs, cudaStr
     }
     sl.h_arena_cap = arena_total;
   }
-  const int grid = large ? sl.grid_large : sl.grid_small;
-  // work list: tiles of every image, cut into per-block items of equal work
   BHeader* hdr = reinterpret_cast<BHeader*>(sl.h_desc + sl.L.hdr);
   BImage* imgs = reinterpret_cast<BImage*>(sl.h_desc + sl.L.imgs);
-  BItem* items = reinterpret_cast<BItem*>(sl.h_desc + sl.L.items);
-  int* starts = reinterpret_cast<int*>(sl.h_desc + sl.L.starts);
-  std::vector<int64_t> tiles(n), cost(n);
-  double total = 0;
+  std::vector<int> ib, ig;
+  std::vector<int64_t> tb, cb, tg, cg;
   size_t off = 0;
   char* abase = static_cast<char*>(sl.arena.p);
   for (int i = 0; i < n; ++i) {
     const ImgSpec& sp = specs[i];
     BImage& im = imgs[i];
+    std::memset(&im, 0, sizeof im);
     im.img = sp.d_img;
     im.n[0] = sp.n[0];
     im.n[1] = sp.n[1];
     im.n[2] = sp.n[2];
     im.bins = sp.bins;
     im.dtype = sp.dtype;
-    im.smem_hist = sp.bins <= kSmemBinsMax ? 1 : 0;
-    im.tiles_x = (sp.n[2] + kT3X - 1) / kT3X;
-    im.tiles_y = (sp.n[1] + kT3Y - 1) / kT3Y;
-    im.zc = std::min<int64_t>(16, std::max<int64_t>(sp.n[0], 1));
-    const int64_t tz = (sp.n[0] + im.zc - 1) / im.zc;
     im.vcec = reinterpret_cast<long long*>(abase + off);
     im.curve = im.vcec + sp.bins;
     im.err = reinterpret_cast<int*>(im.curve + sp.bins);
     off += arena_bytes(sp.bins);
-    tiles[i] = sp.n[0] * sp.n[1] * sp.n[2] > 0 ? im.tiles_x * im.tiles_y * tz : 0;
-    cost[i] = (int64_t)kT3X * kT3Y * (im.zc + 2);
-    total += (double)tiles[i] * cost[i];
-  }
-  const double per_block = total / grid;
-  int n_items = 0, b = 0;
-  double acc = 0;
-  starts[0] = 0;
-  for (int i = 0; i < n; ++i) {
-    int64_t t = 0;
-    while (t < tiles[i]) {
-      const double room = per_block * (b + 1) - acc;
-      int64_t k = std::max<int64_t>(1, (int64_t)(room / cost[i] + 0.999));
-      k = std::min(k, tiles[i] - t);
-      if (n_items >= sl.L.item_cap) return set_err(h, ECC_ERR_CUDA, "work list overflow");
-      items[n_items++] = BItem{i, 0, t, t + k};
-      t += k;
-      acc += (double)k * cost[i];
-      while (b < grid - 1 && acc >= per_block * (b + 1) - 1e-9) starts[++b] = n_items;
+    const int64_t vox = sp.n[0] * sp.n[1] * sp.n[2];
+    if (vox == 0) continue;
+    im.nb = image_nb(h, sp);
+    if (im.nb) {
+      const int64_t eb = sp.dtype == kU8 ? 1 : 2;
+      im.row_pitch = sp.row_pitch > 0 ? sp.row_pitch : sp.n[2] * eb;
+      const int64_t zc = std::min<int64_t>(32, std::max<int64_t>(sp.n[0], 1));
+      im.geo = bits_geo(sp.n[2], sp.n[1], sp.n[0], kBatchBitsWarps, zc);
+      const int64_t width = im.geo.modeB ? 1024 : 32 * im.geo.L;
+      ib.push_back(i);
+      tb.push_back(im.geo.n_tiles);
+      cb.push_back((im.geo.zc + 1) * im.geo.RB * width);
+    } else {
+      im.tiles_x = (sp.n[2] + kT3X - 1) / kT3X;
+      im.tiles_y = (sp.n[1] + kT3Y - 1) / kT3Y;
+      im.zc = std::min<int64_t>(16, std::max<int64_t>(sp.n[0], 1));
+      const int64_t tz = (sp.n[0] + im.zc - 1) / im.zc;
+      ig.push_back(i);
+      tg.push_back(im.tiles_x * im.tiles_y * tz);
+      cg.push_back((int64_t)kT3X * kT3Y * (im.zc + 2) * 12);  // generic: ~12x per voxel
     }
   }
-  while (b < grid) starts[++b] = n_items;
-  // blocks of the launched grid beyond `grid` (the other graph's size) idle
-  for (int j = grid + 1; j <= sl.grid; ++j) starts[j] = n_items;
+  BItem* items_b = reinterpret_cast<BItem*>(sl.h_desc + sl.L.items_b);
+  BItem* items_g = reinterpret_cast<BItem*>(sl.h_desc + sl.L.items_g);
+  int* starts_b = reinterpret_cast<int*>(sl.h_desc + sl.L.starts_b);
+  int* starts_g = reinterpret_cast<int*>(sl.h_desc + sl.L.starts_g);
+  const int nib = partition(ib, tb, cb, sl.L.grid_b, items_b, sl.L.item_cap_b, starts_b);
+  const int nig = partition(ig, tg, cg, sl.L.grid_g, items_g, sl.L.item_cap_g, starts_g);
+  if (nib < 0 || nig < 0) return set_err(h, ECC_ERR_CUDA, "work list overflow");
   hdr->n_images = n;
-  hdr->n_items = n_items;
-  if (wait_ev && (e = cudaStreamWaitEvent(sl.stream, wait_ev, 0)))
-    return cuda_err(h, e, "wait");
-  (void)wait_on;
+  hdr->n_items_bits = nib;
+  hdr->n_items_gen = nig;
+  if (wait_ev && (e = cudaStreamWaitEvent(sl.stream, wait_ev, 0))) return cuda_err(h, e, "wait");
   if ((e = cudaMemcpyAsync(sl.desc.p, sl.h_desc, sl.L.total, cudaMemcpyHostToDevice, sl.stream)))
     return cuda_err(h, e, "upload work list");
   cudaGraphExec_t& ex = large ? sl.exec_large : sl.exec_small;
@@ -335,7 +467,7 @@ int slot_run(ecc_handle* h, Slot& sl, const std::vector<ImgSpec>& specs, cudaStr
     if (e) return cuda_err(h, e, "capture batch graph");
   }
   if ((e = cudaGraphLaunch(ex, sl.stream))) return cuda_err(h, e, "graph launch");
-  h->launches += 3;
+  h->launches += 4;
   if ((e = cudaMemcpyAsync(sl.h_arena, sl.arena.p, arena_total, cudaMemcpyDeviceToHost,
                            sl.stream)) ||
       (e = cudaEventRecord(sl.done, sl.stream)))
@@ -343,7 +475,7 @@ int slot_run(ecc_handle* h, Slot& sl, const std::vector<ImgSpec>& specs, cudaStr
   return ECC_OK;
 }
 
-// Copies image i's curve out of the slot's pinned arena; status from its error word.
+// Image i's curve out of the slot's pinned arena; status from its error word.
 int slot_result(const Slot& sl, const std::vector<ImgSpec>& specs, int i, int64_t** curve) {
   size_t off = 0;
   for (int j = 0; j < i; ++j) off += arena_bytes(specs[j].bins);
@@ -364,6 +496,14 @@ int view3(const int64_t* dims, int ndim, int64_t n[3]) {
   return ECC_OK;
 }
 
+// Row pitch used for device copies of a (1-3D, integer) image: 16-byte
+// multiple when the bit-sliced kernel can take the image, dense otherwise.
+int64_t staged_pitch(const ecc_handle* h, int dtype, int64_t bins, int64_t nx) {
+  const int64_t eb = dtype == kU8 ? 1 : 2;
+  if (h->variant != 1 && bits_nb(dtype, bins)) return (nx * eb + 15) & ~int64_t(15);
+  return nx * eb;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -376,7 +516,9 @@ struct Request {
   int64_t n[3] = {1, 1, 1};
   int dtype = kU8;
   int64_t bins = 256;
-  size_t bytes = 0;
+  size_t bytes = 0;       // dense host bytes
+  int64_t pitch = 0;      // row pitch of the device copy (bytes)
+  size_t dev_bytes = 0;   // bytes of the device copy
   std::vector<unsigned char> host_copy;
   void* d_img = nullptr;
   State state = kQueuedHost;
@@ -406,7 +548,9 @@ struct Server {
 
 namespace {
 
-int64_t request_cost(const Request* r) { return (int64_t)r->bytes + (int64_t)arena_bytes(r->bins); }
+int64_t request_cost(const Request* r) {
+  return (int64_t)r->dev_bytes + (int64_t)arena_bytes(r->bins);
+}
 
 void free_device_image(Server* sv, Request* r) {
   if (r->d_img) {
@@ -420,14 +564,19 @@ void free_device_image(Server* sv, Request* r) {
 bool admit(ecc_handle* h, Server* sv, Request* r) {
   if (sv->bytes_in_use + request_cost(r) > h->cfg.mem_cap_bytes) return false;
   void* d = nullptr;
-  cudaError_t e = cudaMallocAsync(&d, std::max<size_t>(r->bytes, 1), sv->copy_stream);
+  cudaError_t e = cudaMallocAsync(&d, std::max<size_t>(r->dev_bytes, 1), sv->copy_stream);
   if (e) {
     cudaGetLastError();
     return false;
   }
   if (r->bytes) {
-    e = cudaMemcpyAsync(d, r->host_copy.data(), r->bytes, cudaMemcpyHostToDevice,
-                        sv->copy_stream);
+    const size_t dense = dtype_bytes(r->dtype) * (size_t)r->n[2];
+    if ((size_t)r->pitch != dense)
+      e = cudaMemcpy2DAsync(d, (size_t)r->pitch, r->host_copy.data(), dense, dense,
+                            (size_t)(r->n[0] * r->n[1]), cudaMemcpyHostToDevice, sv->copy_stream);
+    else
+      e = cudaMemcpyAsync(d, r->host_copy.data(), r->bytes, cudaMemcpyHostToDevice,
+                          sv->copy_stream);
     if (e) {
       cudaFreeAsync(d, sv->copy_stream);
       r->state = Request::kFailed;
@@ -501,13 +650,14 @@ void serve_loop(ecc_handle* h) {
           continue;
         }
         batch.push_back(r);
-        specs.push_back(ImgSpec{r->d_img, {r->n[0], r->n[1], r->n[2]}, r->dtype, r->bins});
+        specs.push_back(
+            ImgSpec{r->d_img, {r->n[0], r->n[1], r->n[2]}, r->dtype, r->bins, r->pitch});
         it = sv->queue.erase(it);
       }
       if (!batch.empty()) {
         Slot& sl = sv->eng.slots[free_slot];
         cudaEventRecord(sv->copy_ev, sv->copy_stream);  // all admitted copies
-        int rc = slot_run(h, sl, specs, sv->copy_stream, sv->copy_ev);
+        int rc = slot_run(h, sl, specs, sv->copy_ev);
         for (Request* r : batch) {
           r->slot = free_slot;
           r->state = Request::kLaunched;
@@ -636,7 +786,7 @@ int ecc_compute_batch(ecc_handle* h, int n, const ecc_image* images, ecc_result*
     // validate, stage host images into one device buffer
     std::vector<ImgSpec> all(n);
     std::vector<int> ok(n, 0);
-    std::vector<size_t> host_off(n, SIZE_MAX);
+    std::vector<size_t> stage_off(n, SIZE_MAX);
     size_t staged = 0;
     for (int i = 0; i < n; ++i) {
       const ecc_image& im = images[i];
@@ -651,24 +801,39 @@ int ecc_compute_batch(ecc_handle* h, int n, const ecc_image* images, ecc_result*
       outs[i].status = rc;
       if (rc) continue;
       ok[i] = 1;
-      all[i].dtype = im.dtype;
-      all[i].bins = bins;
-      view3(im.dims, im.ndim, all[i].n);
-      all[i].d_img = im.data;
-      if (s.voxels > 0 && !is_device_ptr(h, im.data)) {
-        host_off[i] = staged;
-        staged += (dtype_bytes(im.dtype) * s.voxels + 255) & ~size_t(255);
+      ImgSpec& sp = all[i];
+      sp.dtype = im.dtype;
+      sp.bins = bins;
+      view3(im.dims, im.ndim, sp.n);
+      sp.d_img = im.data;
+      sp.row_pitch = 0;
+      if (s.voxels == 0) continue;
+      // host images, and device images whose rows the bit-sliced kernel
+      // cannot load, are copied into the slot's staging buffer
+      const int64_t dense = (int64_t)dtype_bytes(im.dtype) * sp.n[2];
+      const int64_t pitch = staged_pitch(h, im.dtype, bins, sp.n[2]);
+      const bool dev = is_device_ptr(h, im.data);
+      const bool aligned = (reinterpret_cast<uintptr_t>(im.data) & 15u) == 0 && dense % 16 == 0;
+      const bool eligible = bits_nb(im.dtype, bins) != 0 && h->variant != 1;
+      if (!dev || (eligible && !aligned)) {
+        sp.row_pitch = pitch;
+        stage_off[i] = staged;
+        staged += ((size_t)pitch * (size_t)(sp.n[0] * sp.n[1]) + 255) & ~size_t(255);
       }
     }
     if (staged) {
-      if ((e = h->img.ensure(staged))) return cuda_err(h, e, "batch staging");
+      if ((e = sl.staging.ensure(staged))) return cuda_err(h, e, "batch staging");
       for (int i = 0; i < n; ++i) {
-        if (host_off[i] == SIZE_MAX) continue;
-        const size_t bytes = dtype_bytes(all[i].dtype) * all[i].n[0] * all[i].n[1] * all[i].n[2];
-        char* d = static_cast<char*>(h->img.p) + host_off[i];
-        if ((e = cudaMemcpyAsync(d, images[i].data, bytes, cudaMemcpyHostToDevice, sl.stream)))
+        if (stage_off[i] == SIZE_MAX) continue;
+        ImgSpec& sp = all[i];
+        const size_t dense = dtype_bytes(sp.dtype) * (size_t)sp.n[2];
+        char* d = static_cast<char*>(sl.staging.p) + stage_off[i];
+        const cudaMemcpyKind kind = is_device_ptr(h, images[i].data) ? cudaMemcpyDeviceToDevice
+                                                                      : cudaMemcpyHostToDevice;
+        if ((e = cudaMemcpy2DAsync(d, (size_t)sp.row_pitch, images[i].data, dense, dense,
+                                   (size_t)(sp.n[0] * sp.n[1]), kind, sl.stream)))
           return cuda_err(h, e, "copy batch image");
-        all[i].d_img = d;
+        sp.d_img = d;
       }
     }
     // run in chunks of kMaxBatch valid images
@@ -679,7 +844,7 @@ int ecc_compute_batch(ecc_handle* h, int n, const ecc_image* images, ecc_result*
       const size_t c1 = std::min(idx.size(), c0 + kMaxBatch);
       std::vector<ImgSpec> specs;
       for (size_t j = c0; j < c1; ++j) specs.push_back(all[idx[j]]);
-      int rc = slot_run(h, sl, specs, nullptr, nullptr);
+      int rc = slot_run(h, sl, specs, nullptr);
       if (!rc) rc = wait_event(h, sl.done, 300LL * 1000 * 1000);
       if (rc) return rc;
       for (size_t j = c0; j < c1; ++j) {
@@ -722,6 +887,8 @@ int ecc_submit(ecc_handle* h, const void* image, const int64_t* dims, int ndim, 
     r->bins = default_bins(h, dtype);
     view3(dims, ndim, r->n);
     r->bytes = dtype_bytes(dtype) * (size_t)s.voxels;
+    r->pitch = staged_pitch(h, dtype, r->bins, r->n[2]);
+    r->dev_bytes = (size_t)r->pitch * (size_t)(r->n[0] * r->n[1]);
     r->t_submit = std::chrono::steady_clock::now();
     if (request_cost(r) > h->cfg.mem_cap_bytes) {
       delete r;

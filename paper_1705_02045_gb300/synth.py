@@ -90,6 +90,50 @@ def grf_f32(shape, sigma: float, seed: int) -> np.ndarray:
     return field.astype(np.float32)
 
 
+def _gauss_weights(sigma: float):
+    r = int(4.0 * sigma + 0.5)
+    x = np.arange(-r, r + 1, dtype=np.float64)
+    w = np.exp(-0.5 * (x / sigma) ** 2)
+    return (w / w.sum()).astype(np.float32), r
+
+
+def smooth_int_torch(shape, sigma: float, top: int, seed: int, device="cuda"):
+    """The smoothed-field recipe (white noise -> separable Gaussian, truncated
+    at 4 sigma, reflect border -> linear requantisation to 0..top) computed
+    with torch on `device`, for workloads too large to generate with scipy in
+    a benchmark run. Returns an int32 tensor on `device`. Deterministic for a
+    given seed, device type and torch version (not bit-identical to the numpy
+    generators)."""
+    import torch
+    import torch.nn.functional as F
+
+    g = torch.Generator(device=device).manual_seed(int(seed))
+    x = torch.randn(tuple(shape), generator=g, device=device, dtype=torch.float32)
+    w, r = _gauss_weights(sigma)
+    wt = torch.from_numpy(w).to(device).view(1, 1, -1)
+    for axis in range(x.dim()):
+        n = x.shape[axis]
+        if n <= 1:
+            continue
+        # border extension as scipy's "reflect" (d c b a | a b c d | d c b a)
+        p = np.arange(-r, n + r)
+        while np.any((p < 0) | (p >= n)):
+            p = np.where(p < 0, -p - 1, p)
+            p = np.where(p >= n, 2 * n - p - 1, p)
+        idx = torch.from_numpy(p).to(device)
+        y = x.movedim(axis, -1).contiguous()
+        lead = y.shape[:-1]
+        y = y.reshape(-1, n)
+        out = torch.empty_like(y)
+        for r0 in range(0, y.shape[0], 32768):
+            blk = y[r0:r0 + 32768].index_select(1, idx).unsqueeze(1)
+            out[r0:r0 + 32768] = F.conv1d(blk, wt).squeeze(1)
+        x = out.reshape(*lead, n).movedim(-1, axis)
+    lo, hi = x.min(), x.max()
+    scale = top / (hi - lo) if float(hi - lo) > 0 else 0.0
+    return torch.round((x - lo) * scale).to(torch.int32)
+
+
 def request_mix(n: int, seed: int):
     """Shapes/dtypes of a mixed request stream: 2D:3D = 50:50, side
     log-uniform in [64, 2048] (2D) or [32, 384] (3D), isotropic; dtype uint8

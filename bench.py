@@ -54,13 +54,23 @@ def _barrier(world):
 
 
 def _max_over_ranks(x: float, world: int) -> float:
+    """Max of a per-rank scalar over the process group (NCCL on CUDA, gloo on CPU)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate(voxels_per_rank: int, step_ms: float, world: int):
+    """Replicas: every rank processes its own image; the job's throughput is
+    all ranks' voxels over the slowest rank's step time. Returns
+    (Gvoxel/s, slowest ms per step)."""
+    slowest = _max_over_ranks(step_ms, world)
+    return world * voxels_per_rank / (slowest * 1e-3) / 1e9, slowest
 
 
 class ClockSampler:
@@ -202,7 +212,8 @@ def bench_batched(h, reqs, stream):
 def bench_serving(h, reqs, rate_hz: float, seed: int):
     """Requests submitted at Poisson arrival times (rate_hz), polled to
     completion; latency = submit -> completion as recorded by the library.
-    rate_hz = 0: all submitted at once (saturated)."""
+    rate_hz = 0: all submitted at once (saturated). Request images are in
+    pinned host memory (as from a receive buffer registered with CUDA)."""
     from paper_1705_02045_gb300 import ecc
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate_hz, size=len(reqs)) if rate_hz > 0 else np.zeros(len(reqs))
@@ -226,10 +237,122 @@ def bench_serving(h, reqs, rate_hz: float, seed: int):
         assert st == ecc.ECC_OK
     wall = time.perf_counter() - t0
     lat = np.array([ecc.ecc_request_latency_us(h, rid) for rid in ids]) / 1e3
-    vox = sum(a.size for a, _ in reqs)
+    vox = sum(int(np.prod(a.shape)) for a, _ in reqs)
     return {"requests": len(reqs), "rate_hz": rate_hz, "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
             "gvox_s": vox / wall / 1e9, "wall_s": wall}
+
+
+def workload_stream(args):
+    """14-bit two-phase volume (default 1536 x 3072 x 3072 uint16, 27 GiB,
+    16384 bins): streamed from pinned host memory in z-slabs of 64 planes
+    through a 4 GiB device ring, and fully resident, same bytes; the
+    pinned host->device copy peak measured beside them."""
+    import torch
+    from paper_1705_02045_gb300 import ecc, synth
+    shape = tuple(int(s) for s in args.volume.split(","))
+    nvox = int(np.prod(shape))
+    host = torch.empty(shape, dtype=torch.int16, pin_memory=True)
+    hview = host.numpy().view(np.uint16)
+    t0 = time.perf_counter()
+    for z0, slab in synth.two_phase_u16_slabs(shape, 6.0, synth.SEED_BASE + 2, 64):
+        hview[z0:z0 + slab.shape[0]] = slab
+    gen_s = time.perf_counter() - t0
+    hu = host.view(torch.uint16)
+    # pinned H2D copy peak (4 GiB, best of 3)
+    chunk = hu.reshape(-1)[: (4 << 30) // 2]
+    dbuf = torch.empty(chunk.shape, dtype=torch.int16, device="cuda")
+    best = 1e9
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dbuf.copy_(chunk.view(torch.int16), non_blocking=True)
+        torch.cuda.synchronize()
+        best = min(best, time.perf_counter() - t0)
+    h2d_gbs = chunk.numel() * 2 / best / 1e9
+    del dbuf
+    # streamed
+    h = ecc.ecc_create(device=0, bins=16384, slab_depth=64, ring_bytes=4 << 30)
+    times, curve_s = [], None
+    for rep in range(args.steps + 1):
+        t0 = time.perf_counter()
+        s = ecc.ecc_stream_begin(h, shape, np.uint16)
+        for z0 in range(0, shape[0], 64):
+            ecc.ecc_stream_push_slab(h, s, hu[z0:z0 + 64], z0)
+        curve_s = ecc.ecc_stream_finish(h, s)
+        if rep:
+            times.append(time.perf_counter() - t0)
+    t_stream = min(times)
+    ecc.ecc_destroy(h)
+    # resident
+    d = hu.cuda()
+    h = ecc.ecc_create(device=0, bins=16384)
+    c = torch.empty(16384, dtype=torch.int64, device="cuda")
+    st = torch.cuda.Stream()
+    ecc.ecc_compute_device(h, d, 16384, c, stream=st)
+    st.synchronize()
+    ecc.ecc_set_profiling(h, True)
+    ecc.ecc_profile_read(h)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(st)
+    for _ in range(args.steps):
+        ecc.ecc_compute_device(h, d, 16384, c, stream=st)
+    ev[1].record(st)
+    st.synchronize()
+    t_res = ev[0].elapsed_time(ev[1]) / 1e3 / args.steps
+    kms, n = ecc.ecc_profile_read(h)
+    assert ecc.ecc_device_status(h) == ecc.ECC_OK
+    curve_r = c.cpu().numpy()
+    ecc.ecc_destroy(h)
+    same = bool(np.array_equal(curve_s, curve_r))
+    assert same and curve_r[-1] == 1
+    peak, peak_kind = measured_peak_hbm()
+    kernel_s = kms / max(n, 1) / 1e3
+    print(json.dumps({
+        "metric": METRIC, "workload": "stream", "value": nvox / t_stream / 1e9,
+        "unit": "Gvoxel/s", "n_gpus": 1, "steps": args.steps, "dtype": "u16",
+        "data": "synthetic",
+        "config": {"workload": f"3D {shape} uint16 14-bit two-phase field sigma=6, 16384 bins; "
+                               "z-slabs of 64 planes, 4 GiB ring, pinned host memory"},
+        "streamed": {"seconds": t_stream, "gvox_s": nvox / t_stream / 1e9,
+                     "h2d_gbs": nvox * 2 / t_stream / 1e9,
+                     "fraction_of_h2d_peak": (nvox * 2 / t_stream / 1e9) / h2d_gbs},
+        "resident": {"seconds": t_res, "gvox_s": nvox / t_res / 1e9,
+                     "kernel_s": kernel_s,
+                     "roofline": {"bound": "hbm", "achieved": nvox * 2 / kernel_s / 1e9,
+                                  "peak": peak, "unit": "GB/s",
+                                  "frac": nvox * 2 / kernel_s / 1e9 / peak}},
+        "h2d_peak_gbs": h2d_gbs, "streamed_equals_resident": same,
+        "generation_s": gen_s}), flush=True)
+
+
+def workload_f32(args):
+    """4D 128^4 float32 Gaussian random field (sigma = 3 per axis): pairs,
+    radix sort, reduce-by-key and scan, device-resident input."""
+    import torch
+    from paper_1705_02045_gb300 import ecc, synth
+    shape = tuple(int(s) for s in args.volume.split(","))
+    nvox = int(np.prod(shape))
+    d = synth.grf_f32_torch(shape, 3.0, synth.SEED_BASE + 4).contiguous()
+    h = ecc.ecc_create(device=0)
+    t, chi = ecc.ecc_compute(h, d)
+    times = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        t, chi = ecc.ecc_compute(h, d)
+        times.append(time.perf_counter() - t0)
+    ecc.ecc_destroy(h)
+    assert chi[-1] == 1 and np.all(np.diff(t) > 0)
+    best = min(times)
+    print(json.dumps({
+        "metric": METRIC, "workload": "f32_4d", "value": nvox / best / 1e9,
+        "unit": "Gvoxel/s", "n_gpus": 1, "steps": args.steps, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"4D {shape} float32 Gaussian random field sigma=3, "
+                               "device-resident, exact (threshold, chi) pairs"},
+        "seconds": best, "pairs": int(len(t)),
+        "ms_per_step": best * 1e3}), flush=True)
 
 
 def profile_case(args):
@@ -306,10 +429,25 @@ def main():
                     help="only run this many ecc_compute_device launches (for ncu) and exit")
     ap.add_argument("--profile-shape", default="640,512,512")
     ap.add_argument("--profile-dtype", default="u8", choices=["u8", "u16"])
+    ap.add_argument("--workload", default="resident512",
+                    choices=["resident512", "stream", "f32_4d"],
+                    help="resident512: the headline line; stream / f32_4d: the 14-bit "
+                         "streamed volume and the 4D float image, one line each")
+    ap.add_argument("--volume", default=None, help="shape for --workload stream / f32_4d")
     args = ap.parse_args()
     world, rank, local = _dist()
     if args.profile_launches > 0:
         profile_case(args)
+        return
+    if args.workload != "resident512":
+        args.steps = max(1, min(args.steps, 5))
+    if args.workload == "stream":
+        args.volume = args.volume or "1536,3072,3072"
+        workload_stream(args)
+        return
+    if args.workload == "f32_4d":
+        args.volume = args.volume or "128,128,128,128"
+        workload_f32(args)
         return
     if args.impl == "reference":
         run_reference(args, world, rank)
@@ -369,8 +507,7 @@ def main():
     contrib_ms, n_rec = ecc.ecc_profile_read(h)
     contrib_ms /= max(n_rec, 1)
     ecc.ecc_set_profiling(h, False)
-    step_ms_max = _max_over_ranks(step_ms, world)
-    value = world * nvox / (step_ms_max * 1e-3) / 1e9
+    value, step_ms_max = aggregate(nvox, step_ms, world)
 
     # roofline of the dominant kernel (the contribution kernel)
     peak, peak_kind = measured_peak_hbm()
@@ -427,7 +564,7 @@ def main():
             finally:
                 ecc.ecc_destroy(hb)
             if args.serve_requests > 0:
-                sreqs = reqs[:args.serve_requests]
+                sreqs = [(torch.from_numpy(a).pin_memory(), b) for a, b in reqs[:args.serve_requests]]
                 hs = ecc.ecc_create(device=local)
                 try:
                     sat = bench_serving(hs, sreqs, 0.0, synth.SEED_BASE + 4)
@@ -440,8 +577,9 @@ def main():
                 finally:
                     ecc.ecc_destroy(hs)
                 line["serving"] = {"poisson_0.8x": pois, "saturated": sat,
-                                   "workload": "mixed 2D/3D uint8 / 14-bit uint16 requests, "
-                                               "smoothed fields sigma=2 (synth.request_mix)"}
+                                   "workload": "mixed 2D/3D uint8 / 14-bit uint16 requests in pinned "
+                                               "host memory, smoothed fields sigma=2 "
+                                               "(synth.request_mix)"}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(img)
         print(json.dumps(line), flush=True)

@@ -344,14 +344,13 @@ void slot_free(Slot& sl) {
 // Per-image arena record: vcec[bins], curve[bins], err word.
 size_t arena_bytes(int64_t bins) { return sizeof(long long) * (2 * bins + 1); }
 
-// Bit-sliced kernel for this image? (needs 16-byte aligned rows)
+// Bit-sliced kernel for this image? (any row alignment)
 int image_nb(const ecc_handle* h, const ImgSpec& sp) {
   if (h->variant == 1) return 0;
   const int nb = bits_nb(sp.dtype, sp.bins);
   if (!nb) return 0;
-  const int64_t eb = sp.dtype == kU8 ? 1 : 2;
-  const int64_t pitch = sp.row_pitch > 0 ? sp.row_pitch : sp.n[2] * eb;
-  if ((reinterpret_cast<uintptr_t>(sp.d_img) & 15u) != 0 || (pitch & 15) != 0) return 0;
+  const uintptr_t eb = sp.dtype == kU8 ? 1 : 2;
+  if ((reinterpret_cast<uintptr_t>(sp.d_img) & (eb - 1)) != 0) return 0;
   return nb;
 }
 
@@ -496,12 +495,10 @@ int view3(const int64_t* dims, int ndim, int64_t n[3]) {
   return ECC_OK;
 }
 
-// Row pitch used for device copies of a (1-3D, integer) image: 16-byte
-// multiple when the bit-sliced kernel can take the image, dense otherwise.
-int64_t staged_pitch(const ecc_handle* h, int dtype, int64_t bins, int64_t nx) {
-  const int64_t eb = dtype == kU8 ? 1 : 2;
-  if (h->variant != 1 && bits_nb(dtype, bins)) return (nx * eb + 15) & ~int64_t(15);
-  return nx * eb;
+// Row pitch of device copies of a (1-3D, integer) image: dense (the kernels
+// read rows at any alignment).
+int64_t staged_pitch(const ecc_handle*, int dtype, int64_t, int64_t nx) {
+  return nx * (dtype == kU8 ? 1 : 2);
 }
 
 }  // namespace
@@ -814,8 +811,8 @@ int ecc_compute_batch(ecc_handle* h, int n, const ecc_image* images, ecc_result*
       const int64_t pitch = staged_pitch(h, im.dtype, bins, sp.n[2]);
       const bool dev = is_device_ptr(h, im.data);
       const bool aligned = (reinterpret_cast<uintptr_t>(im.data) & 15u) == 0 && dense % 16 == 0;
-      const bool eligible = bits_nb(im.dtype, bins) != 0 && h->variant != 1;
-      if (!dev || (eligible && !aligned)) {
+      (void)aligned;
+      if (!dev) {
         sp.row_pitch = pitch;
         stage_off[i] = staged;
         staged += ((size_t)pitch * (size_t)(sp.n[0] * sp.n[1]) + 255) & ~size_t(255);
@@ -894,15 +891,58 @@ int ecc_submit(ecc_handle* h, const void* image, const int64_t* dims, int ndim, 
       delete r;
       return set_err(h, ECC_ERR_OOM, "request larger than the device memory cap");
     }
-    // the caller's buffer is copied before returning: into a host copy; the
-    // scheduler moves it to the device when memory is available
-    r->host_copy.resize(r->bytes);
-    if (r->bytes) std::memcpy(r->host_copy.data(), image, r->bytes);
+    // The caller's buffer is copied before returning. Pinned host memory
+    // goes straight to the device if the cap allows (the call waits for that
+    // copy); otherwise the image is copied on the host and the scheduler
+    // moves it to the device when memory is available.
+    bool pinned = false;
+    if (r->bytes) {
+      cudaPointerAttributes at{};
+      if (cudaPointerGetAttributes(&at, image) == cudaSuccess)
+        pinned = at.type == cudaMemoryTypeHost;
+      else
+        cudaGetLastError();
+    }
+    cudaEvent_t copied = nullptr;
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      if (pinned && sv->bytes_in_use + request_cost(r) <= h->cfg.mem_cap_bytes) {
+        void* d = nullptr;
+        cudaError_t e = cudaMallocAsync(&d, r->dev_bytes, sv->copy_stream);
+        if (e == cudaSuccess &&
+            (e = cudaMemcpyAsync(d, image, r->bytes, cudaMemcpyHostToDevice, sv->copy_stream)) ==
+                cudaSuccess &&
+            (e = cudaEventCreateWithFlags(&copied, cudaEventDisableTiming)) == cudaSuccess &&
+            (e = cudaEventRecord(copied, sv->copy_stream)) == cudaSuccess) {
+          r->d_img = d;
+          r->state = Request::kOnDevice;
+          sv->bytes_in_use += request_cost(r);
+        } else {
+          cudaGetLastError();
+          if (d) cudaFreeAsync(d, sv->copy_stream);
+          if (copied) cudaEventDestroy(copied);
+          copied = nullptr;
+        }
+      }
+    }
+    if (copied) {
+      const int rc = wait_event(h, copied, 300LL * 1000 * 1000);
+      cudaEventDestroy(copied);
+      if (rc) {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        free_device_image(sv, r);
+        delete r;
+        return rc;
+      }
+    } else {
+      r->host_copy.resize(r->bytes);
+      if (r->bytes) std::memcpy(r->host_copy.data(), image, r->bytes);
+    }
     {
       std::lock_guard<std::mutex> lk(sv->mu);
       r->id = sv->next_id++;
       sv->all[r->id] = r;
-      admit(h, sv, r);
+      if (r->state == Request::kQueuedHost) admit(h, sv, r);
       sv->queue.push_back(r);
       *req_id = r->id;
     }

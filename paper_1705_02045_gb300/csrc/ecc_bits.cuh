@@ -7,10 +7,11 @@
 // value), computed 32 voxels at a time:
 //
 // * A lane holds 32 consecutive voxels of one row as bit planes: plane k bit j
-//   = bit k of voxel x0 + j, plus an "outside" plane (bit set = the voxel is
-//   outside the image, i.e. +inf: the infinite collar of the paper's Sec. 4).
+//   = bit k of voxel x0 + j.
 // * "N >= C" for 32 voxel pairs is a borrow chain over the planes, one
-//   three-input logic op per plane.
+//   three-input logic op per plane. Voxels outside the image count as +inf
+//   (the infinite collar of the paper's Sec. 4): per-row and x-edge masks
+//   override the comparison in the same final logic op.
 // * Each unordered neighbour pair is compared once: for the 13 neighbour
 //   offsets d that come later in the linear order, G_d[i] = [f(N_i) >= f(C_{i-dx})]
 //   is indexed by the later voxel. The earlier voxel reads its "neighbour
@@ -132,17 +133,22 @@ __device__ __forceinline__ void transpose8(const uint32_t u[8], uint32_t p[8]) {
   for (int k = 0; k < 8; ++k) p[k] = t[k];
 }
 
-// [N >= C] on 32 voxel pairs: no borrow out of N - C (planes LSB first, the
-// outside plane last and most significant).
-template <int NP>
-__device__ __forceinline__ uint32_t ge(const uint32_t* N, const uint32_t* C) {
+// Borrow out of N - C on 32 voxel pairs (planes LSB first): 1 where N < C.
+template <int NB>
+__device__ __forceinline__ uint32_t borrow(const uint32_t* N, const uint32_t* C) {
   uint32_t b = C[0] & ~N[0];
 #pragma unroll
-  for (int k = 1; k < NP; ++k) {
+  for (int k = 1; k < NB; ++k) {
     const uint32_t n = ~N[k], c = C[k];
     b = (n & c) | (n & b) | (c & b);
   }
-  return ~b;
+  return b;
+}
+
+// [N >= C] with voxels outside the image as +inf: 1 where N is outside
+// (nout), else 0 where C is outside (cout), else no borrow. One logic op.
+__device__ __forceinline__ uint32_t gcmp(uint32_t b, uint32_t cout, uint32_t nout) {
+  return (~b & ~cout) | nout;
 }
 
 }  // namespace bits
@@ -155,7 +161,7 @@ template <int NB, int CONV, int HM>
 __device__ void bits_tile(const BitsImg& im, const BitsGeo& geo, int64_t t, uint32_t* pl,
                           uint32_t* g0, uint32_t* g1, int pl_rec, int* hist) {
   using namespace bits;
-  constexpr int NP = NB + 1;            // value planes + outside plane
+  constexpr int NP = NB;                // value planes
   constexpr int EB = NB <= 8 ? 1 : 2;   // bytes per voxel
   constexpr int RAW = 8 * EB;           // raw 32-bit words per lane and row
   const int L = geo.L, RB = geo.RB;
@@ -184,13 +190,21 @@ __device__ void bits_tile(const BitsImg& im, const BitsGeo& geo, int64_t t, uint
   const bool own_lane = (geo.modeB ? (l >= 1 && l <= 30) : true) && x0 >= 0 && x0 < nx;
   const bool own_row = br >= 1 && br <= RB - 2 && row_in;
   const uint32_t dep = (own_lane && own_row) ? xin : 0u;
+  const bool aligned16 =
+      ((reinterpret_cast<uintptr_t>(im.img) | (uintptr_t)row_bytes) & 15u) == 0;
   const uint32_t edgeL = x0 == 0 ? 1u : 0u;
   const uint32_t edgeR = x0 + 32 >= nx ? 0x80000000u : 0u;
 
-  // raw words of plane zp for this lane's 32 voxels (zero if not loaded)
+  // outside masks: xo = bits outside the image in x; cx[dx+1] = outside bits
+  // of the centre row shifted by dx (C'[i] = C[i - dx])
+  const uint32_t xo = ~xin;
+  const uint32_t cx[3] = {(xo >> 1) | edgeR, xo, (xo << 1) | edgeL};
+  const int64_t yup = y + 1, ydn = y - 1;
+  const bool up_in = yup >= 0 && yup < ny, dn_in = ydn >= 0 && ydn < ny;
+
+  // raw words of plane zp for this lane's 32 voxels (unchanged where not
+  // loaded: those voxels are outside and masked)
   auto load_raw = [&](int64_t zp, uint32_t* raw) {
-#pragma unroll
-    for (int i = 0; i < RAW; ++i) raw[i] = 0;
     if (!row_in || zp < 0 || zp >= nz || x0 < 0 || x0 >= nx) return;
     if (zp < im.w_mem_lo || zp >= im.w_mem_hi) {
       atomicOr(im.err, kErrOverflow);
@@ -198,15 +212,29 @@ __device__ void bits_tile(const BitsImg& im, const BitsGeo& geo, int64_t t, uint
     }
     const unsigned char* p =
         im.img + ((size_t)(zp - im.w_mem_lo) * ny + (size_t)y) * row_bytes + (size_t)x0 * EB;
+    if (aligned16) {
 #pragma unroll
-    for (int c = 0; c < RAW / 4; ++c) {
-      if (x0 + c * (16 / EB) < nx) {
-        const uint4 v = __ldg(reinterpret_cast<const uint4*>(p) + c);
-        raw[4 * c] = v.x;
-        raw[4 * c + 1] = v.y;
-        raw[4 * c + 2] = v.z;
-        raw[4 * c + 3] = v.w;
+      for (int c = 0; c < RAW / 4; ++c) {
+        if (x0 + c * (16 / EB) < nx) {
+          const uint4 v = __ldg(reinterpret_cast<const uint4*>(p) + c);
+          raw[4 * c] = v.x;
+          raw[4 * c + 1] = v.y;
+          raw[4 * c + 2] = v.z;
+          raw[4 * c + 3] = v.w;
+        }
       }
+    } else {
+      // rows at any byte alignment: aligned 4-byte words, funnel-shifted;
+      // only words holding at least one byte of this row's voxels are read
+      const uintptr_t pa = reinterpret_cast<uintptr_t>(p);
+      const uint32_t* q = reinterpret_cast<const uint32_t*>(pa & ~uintptr_t(3));
+      const uint32_t sh = (uint32_t)(pa & 3u) * 8u;
+      const int64_t bytes = (nx - x0 >= 32 ? 32 : nx - x0) * EB + (int64_t)(pa & 3u);
+      uint32_t w[RAW + 1];
+#pragma unroll
+      for (int j = 0; j <= RAW; ++j) w[j] = 4 * j < bytes ? __ldg(q + j) : 0u;
+#pragma unroll
+      for (int i = 0; i < RAW; ++i) raw[i] = __funnelshift_r(w[i], w[i + 1], sh);
     }
   };
   // planes of the lane's row at plane zp from its raw words
@@ -231,25 +259,34 @@ __device__ void bits_tile(const BitsImg& im, const BitsGeo& geo, int64_t t, uint
       }
       if (extra & inside) atomicOr(im.err, kErrValue);
     }
-    P[NB] = ~inside;
+    (void)inside;
   };
 
-  uint32_t raw[RAW];
+  uint32_t raw[RAW] = {};
   uint32_t Pz[NP], Ryp[NP], Pn[NP], Pup[NP], Pdn[NP];
   uint32_t Gp[3] = {0u, 0u, 0u};  // own G_(1,0,dx) of the previous step
 
-  // prologue: plane z0 - 1 of the own row, and of the row above
-  load_raw(z0 - 1, raw);
-  make_planes(z0 - 1, raw, Pz);
+  // prologue: the own row and the row above at the first plane zs. A tile at
+  // z0 = 0 has no plane below: its "previous step" exports are zero (the
+  // plane below is outside, every neighbour there comes after), so it starts
+  // at zs = z0; otherwise one priming step at z0 - 1 computes them.
+  const int64_t zs = z0 == 0 ? z0 : z0 - 1;
+  if (z0 == 0) {
+    uint32_t* g1z = g1 + (int)((z0 - 1) & 1) * RB * L * kBitsG1Rec;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) g1z[my * kBitsG1Rec + i] = 0u;
+  }
+  load_raw(zs, raw);
+  make_planes(zs, raw, Pz);
 #pragma unroll
   for (int k = 0; k < NP; ++k) pl[my * pl_rec + k] = Pz[k];
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < NP; ++k) Ryp[k] = pl[up * pl_rec + k];
-  load_raw(z0, raw);
+  load_raw(zs + 1, raw);
   __syncthreads();
 
-  for (int64_t z = z0 - 1; z < z1; ++z) {
+  for (int64_t z = zs; z < z1; ++z) {
     // planes of z + 1 (prefetched one step ago); prefetch z + 2
     make_planes(z + 1, raw, Pn);
     if (z + 2 <= z1) load_raw(z + 2, raw);
@@ -278,23 +315,30 @@ __device__ void bits_tile(const BitsImg& im, const BitsGeo& geo, int64_t t, uint
       Cl[k] = __funnelshift_l(left, Pz[k], 1);
       Cr[k] = __funnelshift_r(Pz[k], right, 1);
     }
-    Cl[NB] |= edgeL;
-    Cr[NB] |= edgeR;
+    // outside masks of this step's rows
+    const bool z_in = z >= 0 && z < nz, z1_in = z + 1 < nz;
+    const uint32_t ALL = 0xFFFFFFFFu;
+    const bool c_in = row_in && z_in;
+    const uint32_t co[3] = {c_in ? cx[0] : ALL, c_in ? cx[1] : ALL, c_in ? cx[2] : ALL};
+    const uint32_t no_z = c_in ? xo : ALL;                  // own row at z
+    const uint32_t no_yp = (up_in && z_in) ? xo : ALL;      // row y+1 at z
+    const uint32_t no1[3] = {(dn_in && z1_in) ? xo : ALL, (row_in && z1_in) ? xo : ALL,
+                             (up_in && z1_in) ? xo : ALL};  // rows y-1..y+1 at z+1
     // the 13 forward comparisons, indexed by the later voxel
-    const uint32_t G001 = ge<NP>(Pz, Cl);
+    const uint32_t G001 = gcmp(borrow<NB>(Pz, Cl), co[2], no_z);
     uint32_t G01[3], G1[3][3];  // [dx+1], [dy+1][dx+1]
-    G01[0] = ge<NP>(Ryp, Cr);
-    G01[1] = ge<NP>(Ryp, Pz);
-    G01[2] = ge<NP>(Ryp, Cl);
-    G1[0][0] = ge<NP>(Pdn, Cr);
-    G1[0][1] = ge<NP>(Pdn, Pz);
-    G1[0][2] = ge<NP>(Pdn, Cl);
-    G1[1][0] = ge<NP>(Pn, Cr);
-    G1[1][1] = ge<NP>(Pn, Pz);
-    G1[1][2] = ge<NP>(Pn, Cl);
-    G1[2][0] = ge<NP>(Pup, Cr);
-    G1[2][1] = ge<NP>(Pup, Pz);
-    G1[2][2] = ge<NP>(Pup, Cl);
+    G01[0] = gcmp(borrow<NB>(Ryp, Cr), co[0], no_yp);
+    G01[1] = gcmp(borrow<NB>(Ryp, Pz), co[1], no_yp);
+    G01[2] = gcmp(borrow<NB>(Ryp, Cl), co[2], no_yp);
+    G1[0][0] = gcmp(borrow<NB>(Pdn, Cr), co[0], no1[0]);
+    G1[0][1] = gcmp(borrow<NB>(Pdn, Pz), co[1], no1[0]);
+    G1[0][2] = gcmp(borrow<NB>(Pdn, Cl), co[2], no1[0]);
+    G1[1][0] = gcmp(borrow<NB>(Pn, Cr), co[0], no1[1]);
+    G1[1][1] = gcmp(borrow<NB>(Pn, Pz), co[1], no1[1]);
+    G1[1][2] = gcmp(borrow<NB>(Pn, Cl), co[2], no1[1]);
+    G1[2][0] = gcmp(borrow<NB>(Pup, Cr), co[0], no1[2]);
+    G1[2][1] = gcmp(borrow<NB>(Pup, Pz), co[1], no1[2]);
+    G1[2][2] = gcmp(borrow<NB>(Pup, Cl), co[2], no1[2]);
     // exports
     uint32_t* g1w = g1 + (int)(z & 1) * RB * L * kBitsG1Rec;
 #pragma unroll

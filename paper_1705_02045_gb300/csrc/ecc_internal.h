@@ -44,6 +44,7 @@ struct LocalArgs {
   int grid = 0;                 // 0 = occupancy-sized persistent grid
   int variant = 0;              // kernel variant (0 = generic key kernel)
   int zc = 0;                   // planes per tile along the marching axis (0 = auto)
+  int warps = 0;                // bit-sliced kernel: warps per block (0 = auto)
   cudaStream_t stream = nullptr;
 };
 

@@ -115,30 +115,14 @@ bool bits_eligible(const ecc_handle* h, const Shape& s, int dtype, int64_t bins)
 
 int stage_image(ecc_handle* h, const void* image, bool on_device, const Shape& s, int dtype,
                 int64_t bins, cudaStream_t st, const void** d_img, int64_t* row_pitch) {
-  const size_t eb = dtype_bytes(dtype);
+  (void)bins;
   *row_pitch = 0;
   *d_img = image;
-  if (s.voxels == 0) return ECC_OK;
-  const size_t dense = eb * (size_t)s.n[s.view - 1];
-  const size_t rows = (size_t)(s.voxels / s.n[s.view - 1]);
+  if (s.voxels == 0 || on_device) return ECC_OK;  // kernels read rows at any alignment
+  const size_t bytes = dtype_bytes(dtype) * (size_t)s.voxels;
   cudaError_t e;
-  if (bits_eligible(h, s, dtype, bins)) {
-    if (on_device && (reinterpret_cast<uintptr_t>(image) & 15u) == 0 && dense % 16 == 0)
-      return ECC_OK;
-    // rows at a 16-byte pitch so that the bit-sliced kernel can load them
-    const size_t pitch = (dense + 15) & ~size_t(15);
-    if ((e = h->img.ensure(pitch * rows))) return cuda_err(h, e, "image buffer");
-    if ((e = cudaMemcpy2DAsync(h->img.p, pitch, image, dense, dense, rows,
-                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                               st)))
-      return cuda_err(h, e, "copy image");
-    *d_img = h->img.p;
-    *row_pitch = (int64_t)pitch;
-    return ECC_OK;
-  }
-  if (on_device) return ECC_OK;
-  if ((e = h->img.ensure(dense * rows))) return cuda_err(h, e, "image buffer");
-  if ((e = cudaMemcpyAsync(h->img.p, image, dense * rows, cudaMemcpyHostToDevice, st)))
+  if ((e = h->img.ensure(bytes))) return cuda_err(h, e, "image buffer");
+  if ((e = cudaMemcpyAsync(h->img.p, image, bytes, cudaMemcpyHostToDevice, st)))
     return cuda_err(h, e, "copy image");
   *d_img = h->img.p;
   return ECC_OK;
@@ -158,12 +142,32 @@ int enqueue_int(ecc_handle* h, const void* d_img, int64_t row_pitch, const Shape
     a.bins = bins;
     a.row_pitch = row_pitch;
     a.variant = h->variant;
+    a.warps = h->bits_warps;
+    a.zc = h->bits_zc;
     a.vcec = d_vcec;
     a.err = h->errw.as<int>();
     a.stream = stream;
     a.w_mem_lo = 0;
     a.w_mem_hi = a.n[0];
     const int64_t step = max_planes_per_launch(s, h->num_sms);
+    // launch shape from the tuner (first image of a shape class tunes it)
+    if (h->tuner && a.view == 3 && bits_nb(dtype, bins) && h->variant != 1 &&
+        h->bits_warps == 0 && h->bits_zc == 0) {
+      LocalArgs t = a;
+      t.w_lo = 0;
+      t.w_hi = std::min(a.n[0], step);
+      const std::string k = Tuner::key(t);
+      TuneChoice c;
+      if (!h->tuner->lookup(k, &c)) {
+        int rc = tune_bits(h, t, &c);
+        if (rc) return rc;
+        if (c.warps > 0) h->tuner->store(k, c);
+        if ((e = cudaMemsetAsync(d_vcec, 0, sizeof(long long) * bins, stream)))
+          return cuda_err(h, e, "memset vcec");
+      }
+      a.warps = c.warps;
+      a.zc = c.zc;
+    }
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (h->prof_on) {
       if ((e = cudaEventCreate(&ev0)) || (e = cudaEventCreate(&ev1)) ||
@@ -347,6 +351,13 @@ int ecc_create(const ecc_config* cfg, ecc_handle** out) {
     if (!std::strcmp(kv, "generic")) h->variant = 1;
     else if (!std::strcmp(kv, "bits")) h->variant = 2;
   }
+  // launch-shape overrides for tuning sweeps of the bit-sliced kernel
+  if (const char* w = std::getenv("ECC_BITS_WARPS")) h->bits_warps = std::atoi(w);
+  if (const char* z = std::getenv("ECC_BITS_ZC")) h->bits_zc = std::atoi(z);
+  if (h->cfg.tuner_cache || std::getenv("ECC_TUNE")) {
+    h->tuner = new (std::nothrow) Tuner();
+    if (h->tuner && h->cfg.tuner_cache) h->tuner->load(h->cfg.tuner_cache);
+  }
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess || h->device < 0 || h->device >= ndev) {
@@ -388,6 +399,7 @@ void ecc_destroy(ecc_handle* h) {
     cudaEventDestroy(pr.first);
     cudaEventDestroy(pr.second);
   }
+  delete h->tuner;
   if (h->h_err) cudaFreeHost(h->h_err);
   if (h->stream) cudaStreamDestroy(h->stream);
   if (h->copy_stream) cudaStreamDestroy(h->copy_stream);

@@ -53,6 +53,23 @@ struct Shape {
 struct BatchEngine;  // batch.cu
 struct Server;       // batch.cu
 
+// Tuned launch shape of the bit-sliced kernel for one shape class (tuner.cu).
+struct TuneChoice {
+  int warps = 0;
+  int zc = 0;
+  float ms = 0.f;
+};
+
+struct Tuner {
+  std::string path;  // JSON-lines cache file ("" = in memory only)
+  std::map<std::string, TuneChoice> table;
+  std::mutex mu;
+  static std::string key(const LocalArgs& a);
+  void load(const std::string& file);
+  bool lookup(const std::string& k, TuneChoice* c);
+  void store(const std::string& k, const TuneChoice& c);
+};
+
 }  // namespace ecc
 
 struct ecc_handle {
@@ -60,6 +77,9 @@ struct ecc_handle {
   int device = 0;
   int num_sms = 0;
   int variant = 0;                     // contribution kernel: 0 auto, 1 generic, 2 bit-sliced
+  int bits_warps = 0;                  // bit-sliced kernel warps per block (0 = auto)
+  int bits_zc = 0;                     // bit-sliced kernel planes per tile (0 = auto)
+  ecc::Tuner* tuner = nullptr;         // launch-shape tuner (tuner_cache set or ECC_TUNE)
   cudaStream_t stream = nullptr;       // compute
   cudaStream_t copy_stream = nullptr;  // host <-> device
   std::string err;
@@ -94,9 +114,9 @@ int enqueue_int(ecc_handle* h, const void* d_img, int64_t row_pitch, const Shape
                 int64_t bins, long long* d_vcec, long long* d_curve, cudaStream_t stream);
 // True when the bit-sliced kernel applies to this shape / dtype / bin count.
 bool bits_eligible(const ecc_handle* h, const Shape& s, int dtype, int64_t bins);
-// Device copy of an image for the contribution kernels: in place if possible,
-// else into the handle's image buffer (rows at a 16-byte pitch when the
-// bit-sliced kernel applies). *row_pitch = 0 means dense rows.
+// Device copy of an image for the contribution kernels: a device image is used
+// in place, a host image is copied (dense) into the handle's image buffer.
+// *row_pitch = 0 means dense rows.
 int stage_image(ecc_handle* h, const void* image, bool on_device, const Shape& s, int dtype,
                 int64_t bins, cudaStream_t st, const void** d_img, int64_t* row_pitch);
 // Bounded wait on an event (host side); ECC_ERR_TIMEOUT after timeout_us.
@@ -106,5 +126,8 @@ cudaError_t launch_local(const LocalArgs& a, int num_sms, int64_t* launches);
 // shared-memory histogram from overflowing.
 int64_t max_planes_per_launch(const Shape& s, int num_sms);
 void serve_shutdown(ecc_handle* h);
+// Times candidate launch shapes of the bit-sliced kernel on this launch.
+int tune_bits(ecc_handle* h, const LocalArgs& base, TuneChoice* best);
+int bits_nb(int dtype, int64_t bins);
 
 }  // namespace ecc

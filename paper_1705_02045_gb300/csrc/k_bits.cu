@@ -86,8 +86,9 @@ int bits_nb(int dtype, int64_t bins) {
 }
 
 // Returns cudaErrorNotSupported when the bit-sliced kernel does not apply
-// (4D view, float values, bins not 256 / 16384 / 65536, rows not 16-byte
-// aligned); the caller then uses the generic kernel.
+// (4D view, float values, bins not 256 / 16384 / 65536, a misaligned uint16
+// pointer); the caller then uses the generic kernel. Rows may start at any
+// byte (16-byte aligned rows take the 128-bit load path).
 cudaError_t launch_local_bits(const LocalArgs& a, int num_sms, int64_t* launches) {
   if (a.view != 3 || a.pairs != nullptr) return cudaErrorNotSupported;
   const int nb = bits_nb(a.dtype, a.bins);
@@ -95,7 +96,7 @@ cudaError_t launch_local_bits(const LocalArgs& a, int num_sms, int64_t* launches
   const int eb = a.dtype == kU8 ? 1 : 2;
   const int64_t nx = a.n[2];
   const int64_t pitch = a.row_pitch > 0 ? a.row_pitch : nx * eb;
-  if ((reinterpret_cast<uintptr_t>(a.img) & 15u) != 0 || (pitch & 15) != 0 || pitch < nx * eb)
+  if (pitch < nx * eb || (reinterpret_cast<uintptr_t>(a.img) & (uintptr_t)(eb - 1)) != 0)
     return cudaErrorNotSupported;
   BitsImg im{};
   im.img = static_cast<const unsigned char*>(a.img);
@@ -111,13 +112,12 @@ cudaError_t launch_local_bits(const LocalArgs& a, int num_sms, int64_t* launches
   im.vcec = a.vcec;
   im.err = a.err;
   // 16 rows per block by default (8 warps of two 16-lane row groups for rows
-  // of <= 512 voxels, 16 warps for rows wider than 1024); a negative zc
-  // selects the warps per block (tuning)
+  // of <= 512 voxels, 16 warps for rows wider than 1024); a.warps overrides
   int L = 1;
   while (L < (nx + 31) / 32 && L < 32) L <<= 1;
   const int R = 32 / L;  // row groups per warp
   int W = std::max(1, std::min(kBitsWarps, 16 / R));
-  if (a.zc < 0) W = (int)std::max<int64_t>(1, std::min<int64_t>(-a.zc, kBitsWarps));
+  if (a.warps > 0) W = std::min(a.warps, kBitsWarps);
   if (W * R < 3) W = (3 + R - 1) / R;  // at least one own row between the collars
   const int64_t zc = a.zc > 0 ? a.zc : 0;
   switch (nb) {

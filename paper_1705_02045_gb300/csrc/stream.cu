@@ -134,14 +134,9 @@ int ecc_stream_begin(ecc_handle* h, const int64_t* dims, int ndim, ecc_dtype dty
     st->s = s;
     st->dtype = dtype;
     st->bins = default_bins(h, dtype);
-    // rows of the slots at a 16-byte pitch when the bit-sliced kernel applies
     st->src_row = dtype_bytes(dtype) * (size_t)s.n[s.view - 1];
     st->rows_per_plane = s.voxels > 0 ? (size_t)(s.voxels / s.n[0] / s.n[s.view - 1]) : 0;
-    size_t slot_row = st->src_row;
-    if (bits_eligible(h, s, dtype, st->bins) && st->src_row % 16 != 0) {
-      slot_row = (st->src_row + 15) & ~size_t(15);
-      st->row_pitch = (int64_t)slot_row;
-    }
+    size_t slot_row = st->src_row;  // dense slot rows (kernels take any alignment)
     st->plane_bytes = slot_row * st->rows_per_plane;
     if (s.voxels == 0) st->plane_bytes = 0;
     st->depth = std::max<int64_t>(1, h->cfg.slab_depth);

@@ -97,13 +97,13 @@ def _gauss_weights(sigma: float):
     return (w / w.sum()).astype(np.float32), r
 
 
-def smooth_int_torch(shape, sigma: float, top: int, seed: int, device="cuda"):
+def smooth_int_torch(shape, sigma: float, top, seed: int, device="cuda"):
     """The smoothed-field recipe (white noise -> separable Gaussian, truncated
     at 4 sigma, reflect border -> linear requantisation to 0..top) computed
     with torch on `device`, for workloads too large to generate with scipy in
-    a benchmark run. Returns an int32 tensor on `device`. Deterministic for a
-    given seed, device type and torch version (not bit-identical to the numpy
-    generators)."""
+    a benchmark run. Returns an int32 tensor on `device` (top = None: the
+    float field before requantisation). Deterministic for a given seed, device
+    type and torch version (not bit-identical to the numpy generators)."""
     import torch
     import torch.nn.functional as F
 
@@ -129,9 +129,75 @@ def smooth_int_torch(shape, sigma: float, top: int, seed: int, device="cuda"):
             blk = y[r0:r0 + 32768].index_select(1, idx).unsqueeze(1)
             out[r0:r0 + 32768] = F.conv1d(blk, wt).squeeze(1)
         x = out.reshape(*lead, n).movedim(-1, axis)
+    if top is None:
+        return x
     lo, hi = x.min(), x.max()
     scale = top / (hi - lo) if float(hi - lo) > 0 else 0.0
     return torch.round((x - lo) * scale).to(torch.int32)
+
+
+def grf_f32_torch(shape, sigma: float, seed: int, device="cuda"):
+    """grf_f32's recipe (normalised Gaussian random field, float32) computed
+    with torch on `device`."""
+    x = smooth_int_torch(shape, sigma, None, seed, device)
+    return x / _filter_std(sigma, len(shape))
+
+
+def two_phase_u16_slabs(shape, sigma: float, seed: int, slab: int, device="cuda"):
+    """The two-phase 14-bit recipe for volumes too large for host-side
+    generation, one z-slab at a time on the GPU (yields (z0, uint16 host
+    array)). Each plane's noise is drawn from its own seeded generator
+    (seed + plane index), and the z-filter of a slab reads sigma * 4 planes
+    of noise on either side (reflected at the volume's ends), so the field is
+    the same as filtering the whole volume at once."""
+    import torch
+    import torch.nn.functional as F
+
+    nz, ny, nx = shape
+    w, r = _gauss_weights(sigma)
+    wt = torch.from_numpy(w).to(device)
+    std = _filter_std(sigma, 3)
+
+    def noise_plane(z):
+        zz = z
+        while zz < 0 or zz >= nz:  # reflect like scipy
+            zz = -zz - 1 if zz < 0 else 2 * nz - zz - 1
+        g = torch.Generator(device=device).manual_seed(int(seed) * 100003 + zz)
+        return torch.randn((ny, nx), generator=g, device=device, dtype=torch.float32)
+
+    def filt_last(x, n):
+        p = np.arange(-r, n + r)
+        while np.any((p < 0) | (p >= n)):
+            p = np.where(p < 0, -p - 1, p)
+            p = np.where(p >= n, 2 * n - p - 1, p)
+        idx = torch.from_numpy(p).to(device)
+        lead = x.shape[:-1]
+        y = x.reshape(-1, n)
+        out = torch.empty_like(y)
+        for r0 in range(0, y.shape[0], 32768):
+            out[r0:r0 + 32768] = F.conv1d(y[r0:r0 + 32768].index_select(1, idx).unsqueeze(1),
+                                          wt.view(1, 1, -1)).squeeze(1)
+        return out.reshape(*lead, n)
+
+    for z0 in range(0, nz, slab):
+        z1 = min(z0 + slab, nz)
+        planes = []
+        for z in range(z0 - r, z1 + r):  # x and y filtered noise planes
+            p = filt_last(noise_plane(z), nx)
+            p = filt_last(p.t().contiguous(), ny).t()
+            planes.append(p)
+        vol = torch.stack(planes)  # (z1 - z0 + 2r, ny, nx)
+        field = torch.zeros((z1 - z0, ny, nx), device=device, dtype=torch.float32)
+        for k in range(2 * r + 1):
+            field += float(w[k]) * vol[k:k + (z1 - z0)]
+        del vol, planes
+        field /= std
+        g = torch.Generator(device=device).manual_seed(int(seed) * 7919 + z0)
+        low = torch.randn(field.shape, generator=g, device=device) * 400.0 + 3000.0
+        high = torch.randn(field.shape, generator=g, device=device) * 900.0 + 11000.0
+        v = torch.where(field < Z_040, low, high)
+        out = torch.clamp(torch.round(v), 0, 16383).to(torch.int16)
+        yield z0, out.cpu().numpy().view(np.uint16)
 
 
 def request_mix(n: int, seed: int):

@@ -96,17 +96,44 @@ def test_bits_rejects_values_above_14_bits():
         ecc.ecc_destroy(h)
 
 
-def test_unaligned_device_pointer_falls_back():
-    """A device image whose rows are not 16-byte aligned goes through the
-    generic kernel under the default choice, with the same result."""
+@pytest.mark.parametrize("offset", [1, 2, 3])
+def test_bits_unaligned_device_rows(offset):
+    """Device images whose rows start at any byte: the bit-sliced kernel's
+    4-byte funnel-shift load path (no staging copy)."""
     import torch
     img = synth.smooth_u8((9, 10, 48), 2.0, S + 15)
-    buf = torch.zeros(img.size + 1, dtype=torch.uint8, device="cuda")
-    view = buf[1:].view(img.shape)
+    buf = torch.zeros(img.size + offset, dtype=torch.uint8, device="cuda")
+    view = buf[offset:].view(img.shape)
     view.copy_(torch.from_numpy(img))
-    h = ecc.ecc_create(device=0)
+    h = _handle("bits")
     try:
         assert np.array_equal(ecc.ecc_compute(h, view), oracle.ecc_int(img, 256, "V"))
+    finally:
+        ecc.ecc_destroy(h)
+
+
+@pytest.mark.parametrize("conv", [0, 1])
+@pytest.mark.parametrize("shape", [(5, 7, 37), (2, 333), (3, 9, 1100), (4, 3, 2077), (35,)],
+                         ids=str)
+def test_bits_odd_widths(conv, shape):
+    """Row widths that are not a multiple of 16 bytes, in row groups and in
+    overlapping warps."""
+    img = synth.uniform_u8(shape, S + 17 + shape[-1])
+    got, _ = _both(img, 256, conv)
+    assert np.array_equal(got, oracle.ecc_int(img, 256, "V" if conv == 0 else "T"))
+
+
+def test_bits_u16_odd_width_unaligned():
+    import torch
+    img = synth.two_phase_u16((4, 5, 47), 1.5, S + 18)
+    if not hasattr(torch, "uint16"):
+        pytest.skip("torch has no uint16")
+    buf = torch.zeros(img.size + 1, dtype=torch.int16, device="cuda")
+    buf[1:].copy_(torch.from_numpy(np.ascontiguousarray(img).ravel().view(np.int16)).cuda())
+    view = buf[1:].view(torch.uint16).view(img.shape)
+    h = _handle("bits", bins=16384)
+    try:
+        assert np.array_equal(ecc.ecc_compute(h, view), oracle.ecc_int(img, 16384, "V"))
     finally:
         ecc.ecc_destroy(h)
 
@@ -137,3 +164,28 @@ def test_bits_full_size_512_cube():
     sub = np.ascontiguousarray(img[:64])
     g_sub, _ = _both(sub, 256, 0)
     assert np.array_equal(g_sub, oracle.ecc_int(sub, 256, "V"))
+
+
+def test_tuner_picks_and_caches_a_launch_shape(tmp_path):
+    """The first image of a shape class tunes the bit-sliced launch shape
+    (extra timed launches) and writes the choice to the cache file; a new
+    handle on the same file reuses it (exactly two launches: contribution and
+    scan). Results are the oracle's either way."""
+    path = str(tmp_path / "tune.jsonl").encode()
+    img = synth.smooth_u8((40, 60, 64), 2.0, S + 19)
+    want = oracle.ecc_int(img, 256, "V")
+    h = ecc.ecc_create(device=0, tuner_cache=path)
+    try:
+        assert np.array_equal(ecc.ecc_compute(h, img), want)
+        tuned_launches = ecc.ecc_launch_count(h)
+    finally:
+        ecc.ecc_destroy(h)
+    lines = open(path.decode()).read().strip().splitlines()
+    assert len(lines) == 1 and '"warps"' in lines[0] and '"zc"' in lines[0]
+    assert tuned_launches > 2
+    h = ecc.ecc_create(device=0, tuner_cache=path)
+    try:
+        assert np.array_equal(ecc.ecc_compute(h, img), want)
+        assert ecc.ecc_launch_count(h) == 2
+    finally:
+        ecc.ecc_destroy(h)

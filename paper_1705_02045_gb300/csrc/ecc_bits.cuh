@@ -133,6 +133,40 @@ __device__ __forceinline__ void transpose8(const uint32_t u[8], uint32_t p[8]) {
   for (int k = 0; k < 8; ++k) p[k] = t[k];
 }
 
+// Bit planes -> bytes, the inverse of transpose8: the three swaps (each an
+// involution, and they commute) and then the byte transposes (involutions).
+__device__ __forceinline__ void untranspose8(const uint32_t p[8], uint32_t u[8]) {
+  uint32_t t[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) t[k] = p[k];
+#pragma unroll
+  for (int st = 0; st < 3; ++st) {
+    const int s = 1 << st;
+    const uint32_t M = st == 0 ? 0x55555555u : st == 1 ? 0x33333333u : 0x0F0F0F0Fu;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      if (r & s) continue;
+      const uint32_t a = t[r], b = t[r | s];
+      t[r] = (a & M) | ((b << s) & ~M);
+      t[r | s] = ((a >> s) & M) | (b & ~M);
+    }
+  }
+  {
+    const uint32_t a = __byte_perm(t[0], t[1], 0x5140), b = __byte_perm(t[0], t[1], 0x7362);
+    const uint32_t c = __byte_perm(t[2], t[3], 0x5140), d = __byte_perm(t[2], t[3], 0x7362);
+    u[0] = __byte_perm(a, c, 0x5410);
+    u[2] = __byte_perm(a, c, 0x7632);
+    u[4] = __byte_perm(b, d, 0x5410);
+    u[6] = __byte_perm(b, d, 0x7632);
+    const uint32_t e = __byte_perm(t[4], t[5], 0x5140), f = __byte_perm(t[4], t[5], 0x7362);
+    const uint32_t g = __byte_perm(t[6], t[7], 0x5140), h = __byte_perm(t[6], t[7], 0x7362);
+    u[1] = __byte_perm(e, g, 0x5410);
+    u[3] = __byte_perm(e, g, 0x7632);
+    u[5] = __byte_perm(f, h, 0x5410);
+    u[7] = __byte_perm(f, h, 0x7632);
+  }
+}
+
 // Borrow out of N - C on 32 voxel pairs (planes LSB first): 1 where N < C.
 template <int NB>
 __device__ __forceinline__ uint32_t borrow(const uint32_t* N, const uint32_t* C) {
@@ -306,12 +340,14 @@ __device__ void bits_tile(const BitsImg& im, const BitsGeo& geo, int64_t t, uint
       Gdn1[i] = g1p[dn * kBitsG1Rec + i];
       Gup1[i] = g1p[up * kBitsG1Rec + 3 + i];
     }
-    // centre row shifted for dx = +1 (C[i-1]) and dx = -1 (C[i+1])
+    // centre row shifted for dx = +1 (C[i-1]) and dx = -1 (C[i+1]). Full-warp
+    // shuffles: a lane at a row-group boundary is at an image x-edge, where
+    // the shifted-in bit is masked as outside (cx, edgeL/edgeR).
     uint32_t Cl[NP], Cr[NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-      const uint32_t left = __shfl_up_sync(FULL, Pz[k], 1, L);
-      const uint32_t right = __shfl_down_sync(FULL, Pz[k], 1, L);
+      const uint32_t left = __shfl_up_sync(FULL, Pz[k], 1);
+      const uint32_t right = __shfl_down_sync(FULL, Pz[k], 1);
       Cl[k] = __funnelshift_l(left, Pz[k], 1);
       Cr[k] = __funnelshift_r(Pz[k], right, 1);
     }
@@ -355,11 +391,11 @@ __device__ void bits_tile(const BitsImg& im, const BitsGeo& geo, int64_t t, uint
     // forward after-bits are G shifted by dx (x-neighbour bit by shuffle)
     auto sh = [&](uint32_t g, int dx) -> uint32_t {
       if (dx == 1) {
-        const uint32_t r = __shfl_down_sync(FULL, g, 1, L);
+        const uint32_t r = __shfl_down_sync(FULL, g, 1);
         return __funnelshift_r(g, r, 1) | edgeR;
       }
       if (dx == -1) {
-        const uint32_t q = __shfl_up_sync(FULL, g, 1, L);
+        const uint32_t q = __shfl_up_sync(FULL, g, 1);
         return __funnelshift_l(q, g, 1) | edgeL;
       }
       return g;
@@ -457,22 +493,46 @@ __device__ void bits_tile(const BitsImg& im, const BitsGeo& geo, int64_t t, uint
       // change = N - 13; zero iff N == 0b01101
       const uint32_t eq13 = ~n4 & n3 & n2 & ~n1 & n0;
       uint32_t nzm = ~eq13 & dep;
+      auto deposit = [&](uint32_t v, int c) {
+        if ((int64_t)v >= im.bins) {
+          atomicOr(im.err, kErrValue);
+        } else if (HM == kBitsSmem) {
+          atomicAdd(&hist[v], c);
+        } else {
+          atomicAdd(reinterpret_cast<unsigned long long*>(im.vcec) + v,
+                    (unsigned long long)(long long)c);
+        }
+      };
+      if (__popc(nzm) >= 8) {
+        // many non-zero changes (noisy data): per-voxel N as bytes by the
+        // inverse transpose, the row's raw values re-read (an L2 hit), and a
+        // fully unrolled deposit with constant byte offsets
+        const uint32_t pn[8] = {n0, n1, n2, n3, n4, 0u, 0u, 0u};
+        uint32_t nbyte[8], rz[RAW];
+        untranspose8(pn, nbyte);
+        load_raw(z, rz);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          if ((nzm >> j) & 1u) {
+            const int N = (int)((nbyte[j >> 2] >> ((j & 3) * 8)) & 31u);
+            const uint32_t v = EB == 1 ? (rz[j >> 2] >> ((j & 3) * 8)) & 0xFFu
+                                       : (rz[j >> 1] >> ((j & 1) * 16)) & 0xFFFFu;
+            deposit(v, N - 13);
+          }
+        }
+        nzm = 0;
+      }
       while (nzm) {
         const int j = __ffs(nzm) - 1;
         nzm &= nzm - 1;
         const int N = (int)(((n0 >> j) & 1u) | (((n1 >> j) & 1u) << 1) | (((n2 >> j) & 1u) << 2) |
                             (((n3 >> j) & 1u) << 3) | (((n4 >> j) & 1u) << 4));
-        uint32_t v = 0;
-#pragma unroll
-        for (int k = 0; k < NB; ++k) v |= ((Pz[k] >> j) & 1u) << k;
-        if ((int64_t)v >= im.bins) {
-          atomicOr(im.err, kErrValue);
-        } else if (HM == kBitsSmem) {
-          atomicAdd(&hist[v], N - 13);
-        } else {
-          atomicAdd(reinterpret_cast<unsigned long long*>(im.vcec) + v,
-                    (unsigned long long)(long long)(N - 13));
-        }
+        // its gray value: the row was read from global memory two steps ago
+        const unsigned char* vp = im.img +
+            ((size_t)(z - im.w_mem_lo) * ny + (size_t)y) * row_bytes + (size_t)(x0 + j) * EB;
+        const uint32_t v = EB == 1 ? (uint32_t)__ldg(vp)
+                                   : (uint32_t)__ldg(reinterpret_cast<const unsigned short*>(vp));
+        deposit(v, N - 13);
       }
     }
 #pragma unroll

@@ -4,6 +4,7 @@
 #include "ecc_bits.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 
 namespace ecc {
 
@@ -14,9 +15,10 @@ namespace {
 // other's barrier waits: measured faster than one block of 16 warps).
 constexpr int kBitsWarps = 16;
 
+// The body of both launch variants: 16-warp blocks (one per SM) and 8-warp
+// blocks bounded to three per SM (more warps to cover barrier waits).
 template <int NB, int CONV, int HM>
-__global__ void __launch_bounds__(32 * kBitsWarps)
-k_bits3(const BitsImg im, const BitsGeo geo, int pl_rec) {
+__device__ __forceinline__ void bits_blocks(const BitsImg& im, const BitsGeo& geo, int pl_rec) {
   extern __shared__ __align__(16) uint32_t sm[];
   const int recs = geo.RB * geo.L;  // = blockDim.x
   uint32_t* pl = sm;
@@ -38,13 +40,26 @@ k_bits3(const BitsImg im, const BitsGeo geo, int pl_rec) {
 }
 
 template <int NB, int CONV, int HM>
+__global__ void __launch_bounds__(32 * kBitsWarps)
+k_bits3(const BitsImg im, const BitsGeo geo, int pl_rec) {
+  bits_blocks<NB, CONV, HM>(im, geo, pl_rec);
+}
+
+template <int NB, int CONV, int HM>
+__global__ void __launch_bounds__(256, 3)
+k_bits3_w8(const BitsImg im, const BitsGeo geo, int pl_rec) {
+  bits_blocks<NB, CONV, HM>(im, geo, pl_rec);
+}
+
+template <int NB, int CONV, int HM>
 cudaError_t launch_t(const BitsImg& im, int W, int64_t zc, int grid_req, int num_sms,
                      cudaStream_t stream, int64_t* launches) {
   constexpr int pl_rec = (NB + 1) | 1;
   const int threads = 32 * W;
   const size_t words = (size_t)threads * (pl_rec + kBitsG0Rec + 2 * kBitsG1Rec);
   const size_t smem = words * 4 + (HM == kBitsSmem ? sizeof(int) * (size_t)im.bins : 0);
-  auto kern = k_bits3<NB, CONV, HM>;
+  auto kern = (W <= 8 && std::getenv("ECC_BITS_LB3")) ? k_bits3_w8<NB, CONV, HM>
+                                                       : k_bits3<NB, CONV, HM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e) return e;
   int per_sm = 0;

@@ -129,6 +129,30 @@ def make_image(seed_offset: int = 1):
     return synth.smooth_u8(SHAPE, SIGMA, synth.SEED_BASE + seed_offset)
 
 
+# Integer logic pipe: 32-bit lanes per SM per clock. The bit-sliced
+# contribution kernel is bound by it (ncu: ALU pipe ~78 % busy at 56 % issue
+# activity, which puts the pipe at half the issue rate: 64 lanes/SM/clock).
+ALU_LANES_PER_SM_CLK = 64
+SM_MAX_MHZ_DEFAULT = 2070.0
+
+
+def alu_ops_per_voxel(nb: int) -> float:
+    """32-bit logic operations per voxel of the bit-sliced formulation, from
+    its formulas (32 voxels per operation): 13 pair comparisons of nb planes
+    plus the outside-mask op each; 12 edge triples (1 op) and 8 vertex boxes
+    (2 ops); the 26-term count (21 full + 3 half adders, 2 ops each); the
+    zero test (3); the byte -> bit-plane transpose (60 for 8 bits; two of
+    them and 16 byte permutes for 16 bits); the centre row shifted left and
+    right (2 nb funnel shifts) and the 10 shifted comparison words (2 ops)."""
+    transpose = 60 if nb <= 8 else 2 * 60 + 16
+    ops = 13 * (nb + 1) + (12 + 16) + 48 + 3 + transpose + 2 * nb + 20
+    return ops / 32.0
+
+
+def alu_peak_tops(num_sms: int, sm_max_mhz) -> float:
+    return num_sms * ALU_LANES_PER_SM_CLK * float(sm_max_mhz or SM_MAX_MHZ_DEFAULT) * 1e6 / 1e12
+
+
 def measured_peak_hbm():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -259,17 +283,22 @@ def workload_stream(args):
         hview[z0:z0 + slab.shape[0]] = slab
     gen_s = time.perf_counter() - t0
     hu = host.view(torch.uint16)
-    # pinned H2D copy peak (4 GiB, best of 3)
-    chunk = hu.reshape(-1)[: (4 << 30) // 2]
-    dbuf = torch.empty(chunk.shape, dtype=torch.int16, device="cuda")
-    best = 1e9
-    for _ in range(3):
+    # pinned H2D copy rate: the first 4 GiB (best of 3), then every 4 GiB
+    # chunk of the whole volume once (the same host pages the stream reads)
+    flat = host.reshape(-1)
+    step = (4 << 30) // 2
+    dbuf = torch.empty(step, dtype=torch.int16, device="cuda")
+
+    def h2d_once(lo):
+        n = min(step, flat.numel() - lo)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        dbuf.copy_(chunk.view(torch.int16), non_blocking=True)
+        dbuf[:n].copy_(flat[lo:lo + n], non_blocking=True)
         torch.cuda.synchronize()
-        best = min(best, time.perf_counter() - t0)
-    h2d_gbs = chunk.numel() * 2 / best / 1e9
+        return n * 2 / (time.perf_counter() - t0) / 1e9
+
+    h2d_gbs = max(h2d_once(0) for _ in range(3))
+    chunk_gbs = [h2d_once(lo) for lo in range(0, flat.numel(), step)]
     del dbuf
     # streamed
     h = ecc.ecc_create(device=0, bins=16384, slab_depth=64, ring_bytes=4 << 30)
@@ -308,6 +337,7 @@ def workload_stream(args):
     assert same and curve_r[-1] == 1
     peak, peak_kind = measured_peak_hbm()
     kernel_s = kms / max(n, 1) / 1e3
+    alu_pk = alu_peak_tops(torch.cuda.get_device_properties(0).multi_processor_count, None)
     print(json.dumps({
         "metric": METRIC, "workload": "stream", "value": nvox / t_stream / 1e9,
         "unit": "Gvoxel/s", "n_gpus": 1, "steps": args.steps, "dtype": "u16",
@@ -319,11 +349,83 @@ def workload_stream(args):
                      "fraction_of_h2d_peak": (nvox * 2 / t_stream / 1e9) / h2d_gbs},
         "resident": {"seconds": t_res, "gvox_s": nvox / t_res / 1e9,
                      "kernel_s": kernel_s,
-                     "roofline": {"bound": "hbm", "achieved": nvox * 2 / kernel_s / 1e9,
-                                  "peak": peak, "unit": "GB/s",
-                                  "frac": nvox * 2 / kernel_s / 1e9 / peak}},
-        "h2d_peak_gbs": h2d_gbs, "streamed_equals_resident": same,
+                     "roofline": {"bound": "alu",
+                                  "achieved": nvox * alu_ops_per_voxel(14) / kernel_s / 1e12,
+                                  "peak": alu_pk, "unit": "Tops/s",
+                                  "frac": nvox * alu_ops_per_voxel(14) / kernel_s / 1e12 / alu_pk,
+                                  "ops_per_voxel": alu_ops_per_voxel(14),
+                                  "hbm": {"achieved": nvox * 2 / kernel_s / 1e9, "peak": peak,
+                                          "unit": "GB/s",
+                                          "frac": nvox * 2 / kernel_s / 1e9 / peak}}},
+        "h2d_peak_gbs": h2d_gbs, "h2d_chunk_gbs": [round(x, 1) for x in chunk_gbs],
+        "streamed_rep_seconds": times, "streamed_equals_resident": same,
         "generation_s": gen_s}), flush=True)
+
+
+def workload_plane(args):
+    """2D 512 x 512 uint8, i.i.d. uniform 0..255, 256 bins: one small image
+    per call, bound by launch latency. Device time of each call (events
+    around it, L2 flushed between calls outside the events), the same call
+    replayed from a CUDA graph, and end to end from pinned host memory."""
+    import torch
+    from paper_1705_02045_gb300 import ecc, synth
+    shape = (512, 512)
+    nvox = shape[0] * shape[1]
+    img = synth.uniform_u8(shape, synth.SEED_BASE + 0)
+    d = torch.from_numpy(img).cuda()
+    c = torch.empty(256, dtype=torch.int64, device="cuda")
+    h = ecc.ecc_create(device=0)
+    st = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(max(args.warmup, 3)):
+        ecc.ecc_compute_device(h, d, 256, c, stream=st)
+    st.synchronize()
+    ref = c.cpu().numpy().copy()
+    assert ref[-1] == 1
+
+    def timed(run):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for a, b in evs:
+            with torch.cuda.stream(st):
+                flush.zero_()
+            a.record(st)
+            run()
+            b.record(st)
+        st.synchronize()
+        return float(np.median([a.elapsed_time(b) for a, b in evs]))
+
+    launches0 = ecc.ecc_launch_count(h)
+    direct_ms = timed(lambda: ecc.ecc_compute_device(h, d, 256, c, stream=st))
+    launches = (ecc.ecc_launch_count(h) - launches0) // args.steps
+    c.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        ecc.ecc_compute_device(h, d, 256, c, stream=st)
+    graph_ms = timed(g.replay)
+    assert np.array_equal(c.cpu().numpy(), ref)
+    hp = torch.from_numpy(img).pin_memory()
+    for _ in range(3):
+        ecc.ecc_compute(h, hp)
+    e2e = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        curve = ecc.ecc_compute(h, hp)
+        e2e.append(time.perf_counter() - t0)
+    assert np.array_equal(curve, ref)
+    ecc.ecc_destroy(h)
+    e2e_s = float(np.median(e2e))
+    print(json.dumps({
+        "metric": METRIC, "workload": "plane512", "value": nvox / (direct_ms * 1e-3) / 1e9,
+        "unit": "Gvoxel/s", "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3),
+        "ms_per_step": direct_ms, "higher_is_better": True, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": "2D 512x512 uint8 i.i.d. uniform 0..255, 256 bins, one image "
+                               "per call, device-resident",
+                   "l2": "256 MiB write between calls, outside the timed events"},
+        "us_per_call": direct_ms * 1e3, "graph_us_per_call": graph_ms * 1e3,
+        "graph_gvox_s": nvox / (graph_ms * 1e-3) / 1e9, "launches_per_call": int(launches),
+        "e2e": {"value": nvox / e2e_s / 1e9, "unit": "Gvoxel/s", "us_per_call": e2e_s * 1e6,
+                "h2d_bytes_per_step": nvox, "d2h_bytes_per_step": 256 * 8}}), flush=True)
 
 
 def workload_f32(args):
@@ -430,14 +532,18 @@ def main():
     ap.add_argument("--profile-shape", default="640,512,512")
     ap.add_argument("--profile-dtype", default="u8", choices=["u8", "u16"])
     ap.add_argument("--workload", default="resident512",
-                    choices=["resident512", "stream", "f32_4d"],
-                    help="resident512: the headline line; stream / f32_4d: the 14-bit "
-                         "streamed volume and the 4D float image, one line each")
+                    choices=["resident512", "stream", "f32_4d", "plane512"],
+                    help="resident512: the headline line; stream / f32_4d / plane512: the "
+                         "14-bit streamed volume, the 4D float image and the 2D 512^2 image, "
+                         "one line each")
     ap.add_argument("--volume", default=None, help="shape for --workload stream / f32_4d")
     args = ap.parse_args()
     world, rank, local = _dist()
     if args.profile_launches > 0:
         profile_case(args)
+        return
+    if args.workload == "plane512":
+        workload_plane(args)
         return
     if args.workload != "resident512":
         args.steps = max(1, min(args.steps, 5))
@@ -536,6 +642,9 @@ def main():
 
     if rank == 0:
         cs = clocks.summary()
+        num_sms = torch.cuda.get_device_properties(local).multi_processor_count
+        alu_peak = alu_peak_tops(num_sms, cs.get("sm_max_mhz"))
+        alu_achieved = nvox * alu_ops_per_voxel(8) / (contrib_ms * 1e-3) / 1e12
         line = {
             "metric": METRIC, "value": value, "unit": "Gvoxel/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms_max,
@@ -544,10 +653,14 @@ def main():
             "config": {"workload": WORKLOAD, "global_batch": world, "voxels_per_gpu": nvox,
                        "bins": BINS, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "256 MiB write between steps, outside the timed events"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "contribution+histogram", "peak_kind": peak_kind,
-                         "kernel_ms": contrib_ms},
+            "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak,
+                         "unit": "Tops/s", "frac": alu_achieved / alu_peak, "traffic": traffic,
+                         "kernel": "contribution+histogram", "kernel_ms": contrib_ms,
+                         "ops_per_voxel": alu_ops_per_voxel(8),
+                         "peak_kind": f"derived: {num_sms} SMs x {ALU_LANES_PER_SM_CLK} "
+                                      "logic lanes/clock x max SM clock",
+                         "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s",
+                                 "frac": achieved / peak, "peak_kind": peak_kind}},
             "e2e": {"value": e2e_value, "unit": "Gvoxel/s", "h2d_bytes_per_step": nvox,
                     "d2h_bytes_per_step": BINS * 8},
             "gpu_launches": int(launches),

@@ -176,7 +176,12 @@ int ecc_compute_batch(ecc_handle* h, int n, const ecc_image* images, ecc_result*
  * copied before the call returns. A scheduler thread admits queued requests
  * while their device memory fits under cfg->mem_cap_bytes, launches each
  * admitted group as one batched launch, and keeps launching newly admitted
- * groups while earlier ones run. *req_id identifies the request. */
+ * groups while earlier ones run. A request whose image is larger than
+ * cfg->ring_bytes is streamed instead (Sec. 3, "Streaming"): slabs of
+ * dims[0] planes pass through a ring of at most cfg->ring_bytes under the
+ * cap, one such request at a time, its partial VCEC kept on the device, while
+ * batches of the other requests go on. ECC_ERR_OOM if the request (or its
+ * ring) cannot fit under the cap. *req_id identifies the request. */
 int ecc_submit(ecc_handle* h, const void* image, const int64_t* dims, int ndim,
                ecc_dtype dtype, uint64_t* req_id);
 

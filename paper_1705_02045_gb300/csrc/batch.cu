@@ -17,13 +17,16 @@
 // their device memory fits under the cap, launches the admitted ones as a
 // batch on one of two slots (two streams), and keeps launching new batches
 // while earlier ones run (continuous batching). Completion is detected by
-// events; results move to the request, device memory returns to the cap.
+// events; results move to the request, device memory returns to the cap. A
+// request larger than the ring is streamed through it in z-slabs on two
+// streams of its own, alongside the batches.
 #include "ecc_bits.cuh"
 #include "ecc_scan.cuh"
 #include "ecc_tile.cuh"
 #include "engine.h"
 
 #include <chrono>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -241,10 +244,33 @@ struct Slot {
   DevBuf staging;  // pitched copies of host / unaligned images
   cudaGraphExec_t exec_small = nullptr, exec_large = nullptr;
   cudaEvent_t done = nullptr;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;  // around the graph, for the online tuner
+  int tune_cand = -1;                      // candidate timed by the last run, or -1
+  double tune_vox = 0;                     // its bit-sliced voxels
+};
+
+// Online tuner of the batched bit-sliced kernel's planes per tile (its
+// z-march depth): while undecided, successive batches take the candidates in
+// turn, each run timed by events around the graph; once every candidate has
+// kTrials runs, the one with the highest voxel rate is kept for the engine's
+// later batches. ECC_BATCH_ZC fixes the depth instead.
+struct BatchTune {
+  static constexpr int kCands = 3;
+  static constexpr int kTrials = 2;
+  static constexpr int kDepth[kCands] = {16, 32, 64};
+  double vox[kCands] = {}, ms[kCands] = {};
+  int runs[kCands] = {};
+  int chosen = -1;
+  int next = 0;
+  int fixed = 0;  // planes per tile from ECC_BATCH_ZC, 0 = tune
 };
 
 struct BatchEngine {
   std::vector<Slot> slots;
+  BatchTune tune;
+  BatchEngine() {
+    if (const char* z = std::getenv("ECC_BATCH_ZC")) tune.fixed = std::max(0, std::atoi(z));
+  }
 };
 
 namespace {
@@ -321,6 +347,7 @@ int slot_init(ecc_handle* h, Slot& sl) {
   sl.L = desc_layout(gb, gg);
   if ((e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking)) ||
       (e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming)) ||
+      (e = cudaEventCreate(&sl.t0)) || (e = cudaEventCreate(&sl.t1)) ||
       (e = sl.desc.ensure(sl.L.total)) || (e = cudaMallocHost(&sl.h_desc, sl.L.total)))
     return cuda_err(h, e, "batch slot");
   std::memset(sl.h_desc, 0, sl.L.total);
@@ -337,6 +364,8 @@ void slot_free(Slot& sl) {
   sl.arena.release();
   sl.staging.release();
   if (sl.done) cudaEventDestroy(sl.done);
+  if (sl.t0) cudaEventDestroy(sl.t0);
+  if (sl.t1) cudaEventDestroy(sl.t1);
   if (sl.stream) cudaStreamDestroy(sl.stream);
   sl = Slot();
 }
@@ -385,9 +414,40 @@ int partition(const std::vector<int>& img_of, const std::vector<int64_t>& tiles,
 // Fills the slot's host descriptors for `specs`, uploads them, replays the
 // captured graph and copies curves and error words to the slot's pinned
 // arena; the slot's `done` event marks completion.
-int slot_run(ecc_handle* h, Slot& sl, const std::vector<ImgSpec>& specs, cudaEvent_t wait_ev) {
+// Books the timing of the slot's previous run (complete: a slot is reused
+// only after its done event) and picks the depth of the next run.
+int tune_depth(BatchTune& t, Slot& sl) {
+  if (sl.tune_cand >= 0) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, sl.t0, sl.t1) == cudaSuccess && ms > 0 && t.chosen < 0) {
+      t.vox[sl.tune_cand] += sl.tune_vox;
+      t.ms[sl.tune_cand] += ms;
+      ++t.runs[sl.tune_cand];
+      bool all = true;
+      for (int i = 0; i < BatchTune::kCands; ++i) all = all && t.runs[i] >= BatchTune::kTrials;
+      if (all) {
+        int best = 0;
+        for (int i = 1; i < BatchTune::kCands; ++i)
+          if (t.vox[i] / t.ms[i] > t.vox[best] / t.ms[best]) best = i;
+        t.chosen = best;
+      }
+    }
+    cudaGetLastError();
+    sl.tune_cand = -1;
+  }
+  if (t.fixed > 0) return t.fixed;
+  if (t.chosen >= 0) return BatchTune::kDepth[t.chosen];
+  sl.tune_cand = t.next;
+  t.next = (t.next + 1) % BatchTune::kCands;
+  return BatchTune::kDepth[sl.tune_cand];
+}
+
+int slot_run(ecc_handle* h, Slot& sl, BatchTune& tune, const std::vector<ImgSpec>& specs,
+             cudaEvent_t wait_ev) {
   cudaError_t e;
   const int n = (int)specs.size();
+  const int depth = tune_depth(tune, sl);
+  double bits_vox = 0;
   bool large = false;
   size_t arena_total = 0;
   for (const ImgSpec& sp : specs) {
@@ -430,8 +490,9 @@ int slot_run(ecc_handle* h, Slot& sl, const std::vector<ImgSpec>& specs, cudaEve
     if (im.nb) {
       const int64_t eb = sp.dtype == kU8 ? 1 : 2;
       im.row_pitch = sp.row_pitch > 0 ? sp.row_pitch : sp.n[2] * eb;
-      const int64_t zc = std::min<int64_t>(32, std::max<int64_t>(sp.n[0], 1));
+      const int64_t zc = std::min<int64_t>(depth, std::max<int64_t>(sp.n[0], 1));
       im.geo = bits_geo(sp.n[2], sp.n[1], sp.n[0], kBatchBitsWarps, zc);
+      bits_vox += (double)vox;
       const int64_t width = im.geo.modeB ? 1024 : 32 * im.geo.L;
       ib.push_back(i);
       tb.push_back(im.geo.n_tiles);
@@ -465,8 +526,14 @@ int slot_run(ecc_handle* h, Slot& sl, const std::vector<ImgSpec>& specs, cudaEve
                                     : capture_graph<kConvV>(sl, large, &ex);
     if (e) return cuda_err(h, e, "capture batch graph");
   }
-  if ((e = cudaGraphLaunch(ex, sl.stream))) return cuda_err(h, e, "graph launch");
+  if ((e = cudaEventRecord(sl.t0, sl.stream)) || (e = cudaGraphLaunch(ex, sl.stream)) ||
+      (e = cudaEventRecord(sl.t1, sl.stream)))
+    return cuda_err(h, e, "graph launch");
   h->launches += 4;
+  if (sl.tune_cand >= 0) {
+    if (bits_vox > 0) sl.tune_vox = bits_vox;
+    else sl.tune_cand = -1;  // nothing to learn from a batch without bit-sliced images
+  }
   if ((e = cudaMemcpyAsync(sl.h_arena, sl.arena.p, arena_total, cudaMemcpyDeviceToHost,
                            sl.stream)) ||
       (e = cudaEventRecord(sl.done, sl.stream)))
@@ -508,7 +575,7 @@ int64_t staged_pitch(const ecc_handle*, int dtype, int64_t, int64_t nx) {
 // ---------------------------------------------------------------------------
 
 struct Request {
-  enum State { kQueuedHost, kOnDevice, kLaunched, kDone, kFailed, kRetired };
+  enum State { kQueuedHost, kOnDevice, kLaunched, kStreaming, kDone, kFailed, kRetired };
   uint64_t id = 0;
   int64_t n[3] = {1, 1, 1};
   int dtype = kU8;
@@ -524,6 +591,33 @@ struct Request {
   int64_t result_bins = 0;
   std::chrono::steady_clock::time_point t_submit, t_done;
   int slot = -1;
+  // streamed requests (device copy larger than the ring): z-slab plan
+  bool streamed = false;
+  int64_t sn[3] = {1, 1, 1};  // view with dims[0] as the marching axis
+  int64_t depth = 0;          // planes per slab
+  int ring_slots = 0;
+  size_t plane_bytes = 0;
+};
+
+// A served request whose image is larger than the ring goes through the
+// device in z-slabs (the streaming scheme of Sec. 3): its planes move from
+// the request's host copy into a ring of slots of (depth + 2) planes on a
+// copy stream, the contribution kernel runs on a slot once the next slot's
+// first plane (its upper collar) is there, and the partial VCEC stays on the
+// device until the last slab. The scheduler advances the job without blocking,
+// so batches of other requests keep launching on the batch slots meanwhile.
+struct SlabJob {
+  Request* r = nullptr;
+  int64_t reserved = 0;      // device bytes counted against the cap
+  void* ring = nullptr;
+  long long* acc = nullptr;  // VCEC (bins), curve (bins), error word
+  long long* h_out = nullptr;  // pinned read-back: curve, error word
+  cudaEvent_t copied[3] = {}, freed[3] = {}, done = nullptr;
+  int64_t z0[3] = {}, nz[3] = {};
+  bool used[3] = {};
+  int64_t next_z = 0, chunks = 0;
+  int pending = -1;
+  bool tail = false;  // last slab, scan and read-back enqueued
 };
 
 struct Server {
@@ -540,6 +634,9 @@ struct Server {
   BatchEngine eng;
   std::vector<std::vector<Request*>> in_flight;  // per slot
   std::vector<std::vector<ImgSpec>> specs;       // per slot
+  // the streamed request in progress (one at a time) and its streams
+  SlabJob* job = nullptr;
+  cudaStream_t job_stream = nullptr, job_copy = nullptr;
   std::string err;
 };
 
@@ -589,6 +686,211 @@ bool admit(ecc_handle* h, Server* sv, Request* r) {
   return true;
 }
 
+// Slab plan of a request (the rule of ecc_stream_begin): dims[0] marches,
+// slabs of cfg.slab_depth planes, shrunk until two slots fit the ring.
+bool plan_slabs(const ecc_handle* h, Request* r, const int64_t* dims, int ndim) {
+  r->sn[0] = dims[0];
+  r->sn[1] = ndim >= 3 ? dims[1] : 1;
+  r->sn[2] = ndim >= 2 ? dims[ndim - 1] : 1;
+  r->plane_bytes = dtype_bytes(r->dtype) * (size_t)(r->sn[1] * r->sn[2]);
+  const int64_t ring_planes = h->cfg.ring_bytes / (int64_t)r->plane_bytes;
+  int64_t depth = std::max<int64_t>(1, h->cfg.slab_depth);
+  if (ring_planes < 2 * (depth + 2)) depth = ring_planes / 2 - 2;
+  if (depth < 1) return false;
+  r->depth = std::min<int64_t>(depth, r->sn[0]);
+  r->ring_slots = (int)std::min<int64_t>(3, ring_planes / (r->depth + 2));
+  return true;
+}
+
+int64_t job_cost(const Request* r) {
+  return (int64_t)r->ring_slots * (r->depth + 2) * (int64_t)r->plane_bytes +
+         (int64_t)(sizeof(long long) * (2 * r->bins + 1));
+}
+
+void job_release(Server* sv, SlabJob* j) {
+  cudaStreamSynchronize(sv->job_stream);
+  cudaStreamSynchronize(sv->job_copy);
+  for (int k = 0; k < 3; ++k) {
+    if (j->copied[k]) cudaEventDestroy(j->copied[k]);
+    if (j->freed[k]) cudaEventDestroy(j->freed[k]);
+  }
+  if (j->done) cudaEventDestroy(j->done);
+  if (j->ring) cudaFreeAsync(j->ring, sv->job_stream);
+  if (j->acc) cudaFreeAsync(j->acc, sv->job_stream);
+  if (j->h_out) cudaFreeHost(j->h_out);
+  sv->bytes_in_use -= j->reserved;
+  delete j;
+}
+
+// Starts the streamed request r if its ring fits under the cap (caller holds
+// mu). Returns false when it has to wait for memory.
+bool job_start(ecc_handle* h, Server* sv, Request* r) {
+  const int64_t cost = job_cost(r);
+  if (sv->bytes_in_use + cost > h->cfg.mem_cap_bytes) return false;
+  SlabJob* j = new (std::nothrow) SlabJob();
+  if (!j) return false;
+  j->r = r;
+  j->reserved = cost;
+  sv->bytes_in_use += cost;
+  const size_t acc_bytes = sizeof(long long) * (2 * r->bins + 1);
+  cudaError_t e = cudaMallocAsync(&j->ring, (size_t)(cost - (int64_t)acc_bytes), sv->job_stream);
+  if (!e) e = cudaMallocAsync(reinterpret_cast<void**>(&j->acc), acc_bytes, sv->job_stream);
+  if (!e) e = cudaMemsetAsync(j->acc, 0, acc_bytes, sv->job_stream);
+  if (!e) e = cudaHostAlloc(reinterpret_cast<void**>(&j->h_out), sizeof(long long) * (r->bins + 1),
+                            cudaHostAllocDefault);
+  for (int k = 0; k < r->ring_slots && !e; ++k)
+    if (!(e = cudaEventCreateWithFlags(&j->copied[k], cudaEventDisableTiming)))
+      e = cudaEventCreateWithFlags(&j->freed[k], cudaEventDisableTiming);
+  if (!e) e = cudaEventCreateWithFlags(&j->done, cudaEventDisableTiming);
+  if (e) {
+    cudaGetLastError();
+    job_release(sv, j);
+    r->state = Request::kFailed;
+    r->status = ECC_ERR_CUDA;
+    r->t_done = std::chrono::steady_clock::now();
+    return true;
+  }
+  r->state = Request::kStreaming;
+  sv->job = j;
+  return true;
+}
+
+// Contribution kernel over the slab held in ring slot k (planes z0 - 1 and,
+// when has_upper, z0 + nz are its collars).
+cudaError_t job_launch(ecc_handle* h, Server* sv, SlabJob& j, int k, bool has_upper) {
+  const Request* r = j.r;
+  LocalArgs a;
+  a.img = static_cast<char*>(j.ring) + (size_t)k * (r->depth + 2) * r->plane_bytes;
+  a.dtype = r->dtype;
+  a.conv = h->cfg.convention;
+  a.view = 3;
+  for (int i = 0; i < 3; ++i) a.n[i] = r->sn[i];
+  a.w_mem_lo = j.z0[k] - 1;
+  a.w_mem_hi = j.z0[k] + j.nz[k] + (has_upper ? 1 : 0);
+  a.bins = r->bins;
+  a.variant = h->variant;
+  a.vcec = j.acc;
+  a.err = reinterpret_cast<int*>(j.acc + 2 * r->bins);
+  a.stream = sv->job_stream;
+  Shape s;
+  s.view = 3;
+  s.n[0] = r->sn[0];
+  s.n[1] = r->sn[1];
+  s.n[2] = r->sn[2];
+  s.voxels = r->sn[0] * r->sn[1] * r->sn[2];
+  const int64_t step = max_planes_per_launch(s, h->num_sms);
+  cudaError_t e = cudaSuccess;
+  for (int64_t w = j.z0[k]; w < j.z0[k] + j.nz[k] && !e; w += step) {
+    a.w_lo = w;
+    a.w_hi = std::min(w + step, j.z0[k] + j.nz[k]);
+    int64_t cnt = 0;
+    e = launch_local(a, h->num_sms, &cnt);
+    h->launches += cnt;
+  }
+  if (!e) e = cudaEventRecord(j.freed[k], sv->job_stream);
+  return e;
+}
+
+// Advances the streamed request without blocking on the GPU: enqueues the
+// slabs whose ring slot is free, then the tail (last slab, scan, read-back),
+// then retires the request once the read-back has landed. The host-to-device
+// copies run with the lock released. Returns true if anything happened.
+bool job_step(ecc_handle* h, Server* sv, std::unique_lock<std::mutex>& lk) {
+  SlabJob& j = *sv->job;
+  Request* r = j.r;
+  cudaError_t e = cudaSuccess;
+  bool progressed = false;
+  if (j.tail) {
+    const cudaError_t q = cudaEventQuery(j.done);
+    if (q == cudaErrorNotReady) return false;
+    r->status = ECC_OK;
+    if (q != cudaSuccess) {
+      cudaGetLastError();
+      r->status = ECC_ERR_CUDA;
+    } else {
+      const int err = static_cast<int>(j.h_out[r->bins]);
+      if (err & kErrValue) r->status = ECC_ERR_VALUE;
+      else if (err & kErrOverflow) r->status = ECC_ERR_CUDA;
+    }
+    if (r->status == ECC_OK) {
+      r->result = static_cast<int64_t*>(std::malloc(sizeof(int64_t) * r->bins));
+      if (r->result) std::memcpy(r->result, j.h_out, sizeof(int64_t) * r->bins);
+      else r->status = ECC_ERR_OOM;
+      r->result_bins = r->bins;
+    }
+    r->state = r->status == ECC_OK ? Request::kDone : Request::kFailed;
+    r->t_done = std::chrono::steady_clock::now();
+    r->host_copy.clear();
+    r->host_copy.shrink_to_fit();
+    sv->job = nullptr;
+    job_release(sv, &j);
+    return true;
+  }
+  const int R = r->ring_slots;
+  while (j.next_z < r->sn[0] && !e) {
+    const int k = (int)(j.chunks % R);
+    if (j.used[k]) {
+      const cudaError_t q = cudaEventQuery(j.freed[k]);
+      if (q == cudaErrorNotReady) break;
+      if (q != cudaSuccess) {
+        e = q;
+        break;
+      }
+    }
+    const int64_t cnz = std::min<int64_t>(r->depth, r->sn[0] - j.next_z);
+    char* base = static_cast<char*>(j.ring) + (size_t)k * (r->depth + 2) * r->plane_bytes;
+    const unsigned char* src = r->host_copy.data() + (size_t)j.next_z * r->plane_bytes;
+    lk.unlock();
+    e = cudaMemcpyAsync(base + r->plane_bytes, src, (size_t)cnz * r->plane_bytes,
+                        cudaMemcpyHostToDevice, sv->job_copy);
+    lk.lock();
+    if (e || (e = cudaEventRecord(j.copied[k], sv->job_copy)) ||
+        (e = cudaStreamWaitEvent(sv->job_stream, j.copied[k], 0)))
+      break;
+    j.z0[k] = j.next_z;
+    j.nz[k] = cnz;
+    j.used[k] = true;
+    if (j.pending >= 0) {
+      const int p = j.pending;
+      char* pbase = static_cast<char*>(j.ring) + (size_t)p * (r->depth + 2) * r->plane_bytes;
+      // collars: this slab's first plane above the previous one, its last below ours
+      if ((e = cudaMemcpyAsync(pbase + (j.nz[p] + 1) * r->plane_bytes, base + r->plane_bytes,
+                               r->plane_bytes, cudaMemcpyDeviceToDevice, sv->job_stream)) ||
+          (e = cudaMemcpyAsync(base, pbase + j.nz[p] * r->plane_bytes, r->plane_bytes,
+                               cudaMemcpyDeviceToDevice, sv->job_stream)) ||
+          (e = job_launch(h, sv, j, p, true)))
+        break;
+    }
+    j.pending = k;
+    ++j.chunks;
+    j.next_z += cnz;
+    progressed = true;
+  }
+  if (!e && j.next_z == r->sn[0]) {
+    int64_t cnt = 0;
+    long long* vcec = j.acc;
+    long long* curve = j.acc + r->bins;
+    if (!(e = job_launch(h, sv, j, j.pending, false)) &&
+        !(e = launch_scan(vcec, curve, r->bins, sv->job_stream, &cnt)) &&
+        !(e = cudaMemcpyAsync(j.h_out, curve, sizeof(long long) * (r->bins + 1),
+                              cudaMemcpyDeviceToHost, sv->job_stream)))
+      e = cudaEventRecord(j.done, sv->job_stream);
+    h->launches += cnt;
+    j.tail = true;
+    progressed = true;
+  }
+  if (e) {
+    cudaGetLastError();
+    r->state = Request::kFailed;
+    r->status = ECC_ERR_CUDA;
+    r->t_done = std::chrono::steady_clock::now();
+    sv->job = nullptr;
+    job_release(sv, &j);
+    return true;
+  }
+  return progressed;
+}
+
 void serve_loop(ecc_handle* h) {
   Server* sv = h->server;
   cudaSetDevice(h->device);
@@ -620,12 +922,30 @@ void serve_loop(ecc_handle* h) {
       progressed = true;
     }
     if (sv->stop) break;
-    // 2. admit host-staged requests in arrival order while memory allows
-    for (Request* r : sv->queue) {
-      if (r->state != Request::kQueuedHost) continue;
+    // 2. admit host-staged requests in arrival order while memory allows; a
+    // streamed request starts when no other one streams and its ring fits
+    for (auto it = sv->queue.begin(); it != sv->queue.end();) {
+      Request* r = *it;
+      if (r->state != Request::kQueuedHost) {
+        ++it;
+        continue;
+      }
+      if (r->streamed) {
+        if (sv->job) {
+          ++it;
+          continue;
+        }
+        if (!job_start(h, sv, r)) break;
+        it = sv->queue.erase(it);
+        progressed = true;
+        continue;
+      }
       if (!admit(h, sv, r)) break;
       progressed = true;
+      ++it;
     }
+    // 2b. advance the streamed request
+    if (sv->job && job_step(h, sv, lk)) progressed = true;
     // 3. launch the admitted requests on a free slot
     int free_slot = -1;
     for (int s = 0; s < nslots; ++s)
@@ -654,7 +974,7 @@ void serve_loop(ecc_handle* h) {
       if (!batch.empty()) {
         Slot& sl = sv->eng.slots[free_slot];
         cudaEventRecord(sv->copy_ev, sv->copy_stream);  // all admitted copies
-        int rc = slot_run(h, sl, specs, sv->copy_ev);
+        int rc = slot_run(h, sl, sv->eng.tune, specs, sv->copy_ev);
         for (Request* r : batch) {
           r->slot = free_slot;
           r->state = Request::kLaunched;
@@ -677,12 +997,17 @@ void serve_loop(ecc_handle* h) {
       sv->cv.notify_all();
       continue;
     }
-    bool busy = false;
+    bool busy = sv->job != nullptr;
     for (int s = 0; s < nslots; ++s) busy = busy || !sv->in_flight[s].empty();
-    if (busy)
-      sv->cv.wait_for(lk, std::chrono::microseconds(20));
-    else
+    if (busy) {
+      // work on the GPU: poll again at once (a timed wait costs the timer
+      // slack, ~50 us, on every completion)
+      lk.unlock();
+      std::this_thread::yield();
+      lk.lock();
+    } else {
       sv->cv.wait_for(lk, std::chrono::milliseconds(5));
+    }
   }
 }
 
@@ -692,6 +1017,8 @@ int server_start(ecc_handle* h) {
   if (!sv) return set_err(h, ECC_ERR_OOM, "server");
   cudaError_t e;
   if ((e = cudaStreamCreateWithFlags(&sv->copy_stream, cudaStreamNonBlocking)) ||
+      (e = cudaStreamCreateWithFlags(&sv->job_stream, cudaStreamNonBlocking)) ||
+      (e = cudaStreamCreateWithFlags(&sv->job_copy, cudaStreamNonBlocking)) ||
       (e = cudaEventCreateWithFlags(&sv->copy_ev, cudaEventDisableTiming))) {
     delete sv;
     return cuda_err(h, e, "server streams");
@@ -731,6 +1058,8 @@ void serve_shutdown(ecc_handle* h) {
     if (sv->th.joinable()) sv->th.join();
     cudaSetDevice(h->device);
     for (Slot& sl : sv->eng.slots) slot_free(sl);
+    if (sv->job) job_release(sv, sv->job);
+    sv->job = nullptr;
     for (auto& kv : sv->all) {
       Request* r = kv.second;
       if (r->d_img) cudaFreeAsync(r->d_img, sv->copy_stream);
@@ -740,6 +1069,8 @@ void serve_shutdown(ecc_handle* h) {
     cudaStreamSynchronize(sv->copy_stream);
     cudaEventDestroy(sv->copy_ev);
     cudaStreamDestroy(sv->copy_stream);
+    cudaStreamDestroy(sv->job_stream);
+    cudaStreamDestroy(sv->job_copy);
     delete sv;
     h->server = nullptr;
   }
@@ -841,7 +1172,7 @@ int ecc_compute_batch(ecc_handle* h, int n, const ecc_image* images, ecc_result*
       const size_t c1 = std::min(idx.size(), c0 + kMaxBatch);
       std::vector<ImgSpec> specs;
       for (size_t j = c0; j < c1; ++j) specs.push_back(all[idx[j]]);
-      int rc = slot_run(h, sl, specs, nullptr);
+      int rc = slot_run(h, sl, h->batch->tune, specs, nullptr);
       if (!rc) rc = wait_event(h, sl.done, 300LL * 1000 * 1000);
       if (rc) return rc;
       for (size_t j = c0; j < c1; ++j) {
@@ -887,7 +1218,14 @@ int ecc_submit(ecc_handle* h, const void* image, const int64_t* dims, int ndim, 
     r->pitch = staged_pitch(h, dtype, r->bins, r->n[2]);
     r->dev_bytes = (size_t)r->pitch * (size_t)(r->n[0] * r->n[1]);
     r->t_submit = std::chrono::steady_clock::now();
-    if (request_cost(r) > h->cfg.mem_cap_bytes) {
+    if ((int64_t)r->dev_bytes > h->cfg.ring_bytes) {
+      // larger than the ring: streamed through it in z-slabs
+      r->streamed = true;
+      if (!plan_slabs(h, r, dims, ndim) || job_cost(r) > h->cfg.mem_cap_bytes) {
+        delete r;
+        return set_err(h, ECC_ERR_OOM, "the slab ring of this request does not fit the cap");
+      }
+    } else if (request_cost(r) > h->cfg.mem_cap_bytes) {
       delete r;
       return set_err(h, ECC_ERR_OOM, "request larger than the device memory cap");
     }
@@ -906,7 +1244,7 @@ int ecc_submit(ecc_handle* h, const void* image, const int64_t* dims, int ndim, 
     cudaEvent_t copied = nullptr;
     {
       std::lock_guard<std::mutex> lk(sv->mu);
-      if (pinned && sv->bytes_in_use + request_cost(r) <= h->cfg.mem_cap_bytes) {
+      if (pinned && !r->streamed && sv->bytes_in_use + request_cost(r) <= h->cfg.mem_cap_bytes) {
         void* d = nullptr;
         cudaError_t e = cudaMallocAsync(&d, r->dev_bytes, sv->copy_stream);
         if (e == cudaSuccess &&
@@ -942,7 +1280,7 @@ int ecc_submit(ecc_handle* h, const void* image, const int64_t* dims, int ndim, 
       std::lock_guard<std::mutex> lk(sv->mu);
       r->id = sv->next_id++;
       sv->all[r->id] = r;
-      if (r->state == Request::kQueuedHost) admit(h, sv, r);
+      if (r->state == Request::kQueuedHost && !r->streamed) admit(h, sv, r);
       sv->queue.push_back(r);
       *req_id = r->id;
     }

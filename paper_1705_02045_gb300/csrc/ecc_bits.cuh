@@ -508,16 +508,33 @@ __device__ void bits_tile(const BitsImg& im, const BitsGeo& geo, int64_t t, uint
         // inverse transpose, the row's raw values re-read (an L2 hit), and a
         // fully unrolled deposit with constant byte offsets
         const uint32_t pn[8] = {n0, n1, n2, n3, n4, 0u, 0u, 0u};
-        uint32_t nbyte[8], rz[RAW];
+        uint32_t nbyte[8];
         untranspose8(pn, nbyte);
-        load_raw(z, rz);
+        const unsigned char* rp = im.img + ((size_t)(z - im.w_mem_lo) * ny + (size_t)y) * row_bytes +
+                                  (size_t)x0 * EB;
+        // two halves of 16 voxels keep fewer raw words live
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          if ((nzm >> j) & 1u) {
-            const int N = (int)((nbyte[j >> 2] >> ((j & 3) * 8)) & 31u);
-            const uint32_t v = EB == 1 ? (rz[j >> 2] >> ((j & 3) * 8)) & 0xFFu
-                                       : (rz[j >> 1] >> ((j & 1) * 16)) & 0xFFFFu;
-            deposit(v, N - 13);
+        for (int hf = 0; hf < 2; ++hf) {
+          uint32_t rz[RAW / 2];
+          const uintptr_t pa = reinterpret_cast<uintptr_t>(rp) + (uintptr_t)(hf * 16 * EB);
+          const uint32_t* q = reinterpret_cast<const uint32_t*>(pa & ~uintptr_t(3));
+          const uint32_t sh8 = (uint32_t)(pa & 3u) * 8u;
+          uint32_t w[RAW / 2 + 1];
+          const int64_t left = nx - x0 - hf * 16;
+          const int64_t bytes = (left >= 16 ? 16 : (left > 0 ? left : 0)) * EB + (int64_t)(pa & 3u);
+#pragma unroll
+          for (int i = 0; i <= RAW / 2; ++i) w[i] = 4 * i < bytes ? __ldg(q + i) : 0u;
+#pragma unroll
+          for (int i = 0; i < RAW / 2; ++i) rz[i] = __funnelshift_r(w[i], w[i + 1], sh8);
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            const int j = hf * 16 + jj;
+            if ((nzm >> j) & 1u) {
+              const int N = (int)((nbyte[j >> 2] >> ((j & 3) * 8)) & 31u);
+              const uint32_t v = EB == 1 ? (rz[jj >> 2] >> ((jj & 3) * 8)) & 0xFFu
+                                         : (rz[jj >> 1] >> ((jj & 1) * 16)) & 0xFFFFu;
+              deposit(v, N - 13);
+            }
           }
         }
         nzm = 0;

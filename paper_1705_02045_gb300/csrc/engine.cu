@@ -167,6 +167,7 @@ int enqueue_int(ecc_handle* h, const void* d_img, int64_t row_pitch, const Shape
       }
       a.warps = c.warps;
       a.zc = c.zc;
+      a.hist = c.hist;
     }
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (h->prof_on) {
@@ -204,7 +205,12 @@ int wait_event(ecc_handle* h, cudaEvent_t ev, int64_t timeout_us) {
                         std::chrono::steady_clock::now() - t0).count();
     if (timeout_us >= 0 && dt >= timeout_us)
       return set_err(h, ECC_ERR_TIMEOUT, "wait ran out after %lld us", (long long)dt);
-    std::this_thread::sleep_for(std::chrono::microseconds(dt < 1000 ? 5 : 100));
+    // spin for the first 2 ms (a sleep costs the timer slack, ~50 us), then
+    // poll every 100 us
+    if (dt < 2000)
+      std::this_thread::yield();
+    else
+      std::this_thread::sleep_for(std::chrono::microseconds(100));
   }
 }
 
@@ -401,6 +407,7 @@ void ecc_destroy(ecc_handle* h) {
   }
   delete h->tuner;
   if (h->h_err) cudaFreeHost(h->h_err);
+  if (h->h_curve) cudaFreeHost(h->h_curve);
   if (h->stream) cudaStreamDestroy(h->stream);
   if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   delete h;
@@ -477,11 +484,21 @@ int ecc_compute(ecc_handle* h, const void* image, const int64_t* dims, int ndim,
     out->bins = bins;
     out->curve = static_cast<int64_t*>(std::malloc(sizeof(int64_t) * bins));
     if (!out->curve) return set_err(h, ECC_ERR_OOM, "host curve");
-    if ((e = cudaMemcpyAsync(out->curve, h->curve.p, sizeof(int64_t) * bins,
+    // through a pinned buffer: an asynchronous copy, one wait for both reads
+    if ((size_t)bins > h->h_curve_cap) {
+      if (h->h_curve) cudaFreeHost(h->h_curve);
+      h->h_curve = nullptr;
+      h->h_curve_cap = 0;
+      if ((e = cudaMallocHost(&h->h_curve, sizeof(int64_t) * bins)))
+        return cuda_err(h, e, "pinned curve");
+      h->h_curve_cap = (size_t)bins;
+    }
+    if ((e = cudaMemcpyAsync(h->h_curve, h->curve.p, sizeof(int64_t) * bins,
                              cudaMemcpyDeviceToHost, h->stream)))
       return cuda_err(h, e, "copy curve");
     int word = 0;
     if ((rc = read_err_word(h, h->stream, &word))) return rc;
+    std::memcpy(out->curve, h->h_curve, sizeof(int64_t) * bins);
     if ((rc = err_word_status(h, word))) {
       ecc_result_free(out);
       return rc;

@@ -58,6 +58,7 @@ struct TuneChoice {
   int warps = 0;
   int zc = 0;
   float ms = 0.f;
+  int hist = 0;  // LocalArgs::hist
 };
 
 struct Tuner {
@@ -90,6 +91,8 @@ struct ecc_handle {
   ecc::DevBuf img, vcec, curve, errw, pairs, pair_count, tmp, out_keys, out_chi, out_count;
   ecc::DevBuf batch_desc, batch_items, batch_vcec, batch_curve;
   int* h_err = nullptr;                 // pinned scalar for error readback
+  int64_t* h_curve = nullptr;           // pinned staging of integer curves
+  size_t h_curve_cap = 0;               // entries of h_curve
 
   // instrumentation: event pairs around contribution kernels
   bool prof_on = false;

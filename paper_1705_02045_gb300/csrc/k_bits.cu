@@ -15,8 +15,8 @@ namespace {
 // other's barrier waits: measured faster than one block of 16 warps).
 constexpr int kBitsWarps = 16;
 
-// The body of both launch variants: 16-warp blocks (one per SM) and 8-warp
-// blocks bounded to three per SM (more warps to cover barrier waits).
+// Persistent blocks over the tiles of one image, each with a private
+// histogram added to the VCEC at the end.
 template <int NB, int CONV, int HM>
 __device__ __forceinline__ void bits_blocks(const BitsImg& im, const BitsGeo& geo, int pl_rec) {
   extern __shared__ __align__(16) uint32_t sm[];
@@ -46,20 +46,13 @@ k_bits3(const BitsImg im, const BitsGeo geo, int pl_rec) {
 }
 
 template <int NB, int CONV, int HM>
-__global__ void __launch_bounds__(256, 3)
-k_bits3_w8(const BitsImg im, const BitsGeo geo, int pl_rec) {
-  bits_blocks<NB, CONV, HM>(im, geo, pl_rec);
-}
-
-template <int NB, int CONV, int HM>
 cudaError_t launch_t(const BitsImg& im, int W, int64_t zc, int grid_req, int num_sms,
                      cudaStream_t stream, int64_t* launches) {
   constexpr int pl_rec = (NB + 1) | 1;
   const int threads = 32 * W;
   const size_t words = (size_t)threads * (pl_rec + kBitsG0Rec + 2 * kBitsG1Rec);
   const size_t smem = words * 4 + (HM == kBitsSmem ? sizeof(int) * (size_t)im.bins : 0);
-  auto kern = (W <= 8 && std::getenv("ECC_BITS_LB3")) ? k_bits3_w8<NB, CONV, HM>
-                                                       : k_bits3<NB, CONV, HM>;
+  auto kern = k_bits3<NB, CONV, HM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e) return e;
   int per_sm = 0;
@@ -81,9 +74,9 @@ cudaError_t launch_t(const BitsImg& im, int W, int64_t zc, int grid_req, int num
 }
 
 template <int NB>
-cudaError_t launch_nb(const BitsImg& im, int conv, int W, int64_t zc, int grid, int num_sms,
-                      cudaStream_t st, int64_t* launches) {
-  const bool smem_hist = im.bins <= kSmemBinsMax;
+cudaError_t launch_nb(const BitsImg& im, int conv, int hist, int W, int64_t zc, int grid,
+                      int num_sms, cudaStream_t st, int64_t* launches) {
+  const bool smem_hist = im.bins <= kSmemBinsMax && hist != 2;
   if (conv == kConvT)
     return smem_hist ? launch_t<NB, kConvT, kBitsSmem>(im, W, zc, grid, num_sms, st, launches)
                      : launch_t<NB, kConvT, kBitsGlobal>(im, W, zc, grid, num_sms, st, launches);
@@ -136,9 +129,9 @@ cudaError_t launch_local_bits(const LocalArgs& a, int num_sms, int64_t* launches
   if (W * R < 3) W = (3 + R - 1) / R;  // at least one own row between the collars
   const int64_t zc = a.zc > 0 ? a.zc : 0;
   switch (nb) {
-    case 8: return launch_nb<8>(im, a.conv, W, zc, a.grid, num_sms, a.stream, launches);
-    case 14: return launch_nb<14>(im, a.conv, W, zc, a.grid, num_sms, a.stream, launches);
-    default: return launch_nb<16>(im, a.conv, W, zc, a.grid, num_sms, a.stream, launches);
+    case 8: return launch_nb<8>(im, a.conv, a.hist, W, zc, a.grid, num_sms, a.stream, launches);
+    case 14: return launch_nb<14>(im, a.conv, a.hist, W, zc, a.grid, num_sms, a.stream, launches);
+    default: return launch_nb<16>(im, a.conv, a.hist, W, zc, a.grid, num_sms, a.stream, launches);
   }
 }
 

@@ -3,9 +3,11 @@
 // For each shape class (value bits, lanes per row group, convention, and the
 // base-2 logarithms of the row count and of the plane count) the first image
 // of the class times a few launch shapes -- warps per block (rows per block)
-// and planes per tile -- on its own data, keeps the fastest, and reuses it
-// for every later image of the class. With ecc_config.tuner_cache set, the
-// table is read from and appended to that file (one JSON object per line).
+// and planes per tile, then block-private shared-memory histograms against
+// direct global atomics for the fastest shape -- on its own data, keeps the
+// fastest, and reuses it for every later image of the class. With
+// ecc_config.tuner_cache set, the table is read from and appended to that
+// file (one JSON object per line).
 #include "engine.h"
 
 #include <cmath>
@@ -49,12 +51,12 @@ void Tuner::load(const std::string& file) {
   char line[256];
   while (std::fgets(line, sizeof line, f)) {
     char k[96] = {0};
-    int w = 0, z = 0;
+    int w = 0, z = 0, hm = 0;
     float ms = 0;
-    if (std::sscanf(line, " {\"key\": \"%95[^\"]\", \"warps\": %d, \"zc\": %d, \"ms\": %f", k, &w,
-                    &z, &ms) == 4 &&
-        w > 0 && z > 0)
-      table[k] = TuneChoice{w, z, ms};
+    const int got =
+        std::sscanf(line, " {\"key\": \"%95[^\"]\", \"warps\": %d, \"zc\": %d, \"ms\": %f, \"hist\": %d",
+                    k, &w, &z, &ms, &hm);
+    if (got >= 4 && w > 0 && z > 0) table[k] = TuneChoice{w, z, ms, got == 5 ? hm : 0};
   }
   std::fclose(f);
 }
@@ -72,8 +74,8 @@ void Tuner::store(const std::string& k, const TuneChoice& c) {
   table[k] = c;
   if (path.empty()) return;
   if (FILE* f = std::fopen(path.c_str(), "a")) {
-    std::fprintf(f, "{\"key\": \"%s\", \"warps\": %d, \"zc\": %d, \"ms\": %.6f}\n", k.c_str(),
-                 c.warps, c.zc, c.ms);
+    std::fprintf(f, "{\"key\": \"%s\", \"warps\": %d, \"zc\": %d, \"ms\": %.6f, \"hist\": %d}\n",
+                 k.c_str(), c.warps, c.zc, c.ms, c.hist);
     std::fclose(f);
   }
 }
@@ -91,6 +93,18 @@ int tune_bits(ecc_handle* h, const LocalArgs& base, TuneChoice* best) {
   best->warps = 0;
   best->zc = 0;
   int rc = ECC_OK;
+  // one warm launch, then one timed launch of a candidate
+  auto time_one = [&](const LocalArgs& a, float* ms) -> int {
+    int64_t cnt = 0;
+    if ((e = launch_local(a, h->num_sms, &cnt)) || (e = cudaEventRecord(e0, a.stream)) ||
+        (e = launch_local(a, h->num_sms, &cnt)) || (e = cudaEventRecord(e1, a.stream)))
+      return cuda_err(h, e, "tuner launch");
+    h->launches += cnt;
+    int r = wait_event(h, e1, 300LL * 1000 * 1000);
+    if (r) return r;
+    if ((e = cudaEventElapsedTime(ms, e0, e1))) return cuda_err(h, e, "tuner timing");
+    return ECC_OK;
+  };
   for (int W : {4, 8, 16}) {
     if (W * R < 3 || W * R > 512) continue;
     for (int zc : {16, 32, 64, 128}) {
@@ -98,22 +112,21 @@ int tune_bits(ecc_handle* h, const LocalArgs& base, TuneChoice* best) {
       LocalArgs a = base;
       a.warps = W;
       a.zc = zc;
-      int64_t cnt = 0;
-      if ((e = launch_local(a, h->num_sms, &cnt)) || (e = cudaEventRecord(e0, a.stream)) ||
-          (e = launch_local(a, h->num_sms, &cnt)) || (e = cudaEventRecord(e1, a.stream))) {
-        rc = cuda_err(h, e, "tuner launch");
-        break;
-      }
-      h->launches += cnt;
-      if ((rc = wait_event(h, e1, 300LL * 1000 * 1000))) break;
+      a.hist = 0;
       float ms = 0;
-      if ((e = cudaEventElapsedTime(&ms, e0, e1))) {
-        rc = cuda_err(h, e, "tuner timing");
-        break;
-      }
-      if (ms < best->ms) *best = TuneChoice{W, zc, ms};
+      if ((rc = time_one(a, &ms))) break;
+      if (ms < best->ms) *best = TuneChoice{W, zc, ms, 0};
     }
     if (rc) break;
+  }
+  // histogram privatisation for the fastest shape: shared memory or global
+  if (!rc && best->warps > 0 && base.bins <= kSmemBinsMax) {
+    LocalArgs a = base;
+    a.warps = best->warps;
+    a.zc = best->zc;
+    a.hist = 2;
+    float ms = 0;
+    if (!(rc = time_one(a, &ms)) && ms < best->ms) *best = TuneChoice{best->warps, best->zc, ms, 2};
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

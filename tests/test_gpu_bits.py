@@ -182,6 +182,7 @@ def test_tuner_picks_and_caches_a_launch_shape(tmp_path):
         ecc.ecc_destroy(h)
     lines = open(path.decode()).read().strip().splitlines()
     assert len(lines) == 1 and '"warps"' in lines[0] and '"zc"' in lines[0]
+    assert '"hist": 0' in lines[0] or '"hist": 2' in lines[0]
     assert tuned_launches > 2
     h = ecc.ecc_create(device=0, tuner_cache=path)
     try:

@@ -268,3 +268,56 @@ def test_destroy_with_requests_in_flight(lib):
     for i in range(20):
         ecc.ecc_submit(h, synth.uniform_u8((40, 40, 40), S + 50 + i))
     ecc.ecc_destroy(h)  # cancels cleanly
+
+
+def test_serve_streams_requests_larger_than_the_ring(lib):
+    """Requests larger than the ring go through it in z-slabs (3D: planes of
+    dims[0]; 2D: rows) while the small requests around them are batched; every
+    result equals the one-shot computation and the oracle."""
+    big3 = synth.two_phase_u16((60, 40, 130), 1.5, S + 50)        # 624000 B
+    big2 = synth.smooth_int((700, 500), 2.0, 16383, S + 51, np.uint16)  # 700000 B
+    small = _mixed_images(24, S + 52, max2d=150, max3d=40)
+    order = [(big3, 16384)] + small[:12] + [(big2, 16384)] + small[12:]
+    h = ecc.ecc_create(device=0, bins=16384, ring_bytes=256 * 1024, slab_depth=8,
+                       mem_cap_bytes=64 << 20)
+    try:
+        alone = [ecc.ecc_compute(h, img) for img, _ in order]
+        ids = [ecc.ecc_submit(h, img) for img, _ in order]
+        got = []
+        for rid in ids:
+            st, curve = ecc.ecc_poll(h, rid, timeout_us=120_000_000)
+            assert st == ecc.ECC_OK
+            got.append(curve)
+    finally:
+        ecc.ecc_destroy(h)
+    for (img, _), a, g in zip(order, alone, got):
+        assert np.array_equal(g, a)
+    assert np.array_equal(got[0], oracle.ecc_int(big3, 16384, "V"))
+    assert np.array_equal(got[13], oracle.ecc_int(big2, 16384, "V"))
+
+
+def test_serve_streamed_request_errors(lib):
+    """A value >= bins inside a streamed request fails that request only; a
+    ring that cannot fit under the cap is refused at submit."""
+    bad = synth.two_phase_u16((30, 40, 130), 1.5, S + 53)
+    bad[17, 5, 9] = 20000
+    ok = synth.smooth_u8((20, 30, 40), 2.0, S + 54)
+    h = ecc.ecc_create(device=0, bins=16384, ring_bytes=128 * 1024, slab_depth=4,
+                       mem_cap_bytes=16 << 20)
+    try:
+        r_bad = ecc.ecc_submit(h, bad)
+        r_ok = ecc.ecc_submit(h, ok)
+        with pytest.raises(ecc.EccError) as ei:
+            ecc.ecc_poll(h, r_bad, timeout_us=120_000_000)
+        assert ei.value.status == ecc.ECC_ERR_VALUE
+        st, curve = ecc.ecc_poll(h, r_ok, timeout_us=120_000_000)
+        assert st == ecc.ECC_OK and np.array_equal(curve, oracle.ecc_int(ok, 16384, "V"))
+    finally:
+        ecc.ecc_destroy(h)
+    h = ecc.ecc_create(device=0, ring_bytes=1 << 20, mem_cap_bytes=512 * 1024)
+    try:
+        with pytest.raises(ecc.EccError) as ei:
+            ecc.ecc_submit(h, np.zeros((64, 128, 256), np.uint8))  # 2 MiB, ring over the cap
+        assert ei.value.status == ecc.ECC_ERR_OOM
+    finally:
+        ecc.ecc_destroy(h)

@@ -24,5 +24,7 @@ from .ecc_oracle import (  # noqa: F401
     ecc_int,
     ecc_from_vcec,
     ecc_pairs_float,
+    quantize_f32,
+    ecc_quantized,
     cell_counts,
 )

@@ -23,7 +23,10 @@ Images"):
 * Integer range (Sec. 3, "Range of Values"): thresholds t in {0..m-1}.
 * Other ranges (Sec. 3, "Other Ranges of Gray Values"): for float images the
   VCEC is keyed by the value itself (the paper's hash map); output is the list
-  of (t, chi(K_t)) at the values t where a_t != 0, ascending.
+  of (t, chi(K_t)) at the values t where a_t != 0, ascending. The same passage
+  offers the alternative of transforming the values (shift, scale, round) into
+  {0..m-1} and running the integer algorithm: `quantize_f32` is that
+  transform, `ecc_quantized` its curve.
 
 Convention "T" is the alternative the same section names in a footnote: the
 dual complex, voxels as vertices, lower-star filtration. A cell is a box of
@@ -224,6 +227,41 @@ def ecc_pairs_float(img: np.ndarray, convention: str = "V"):
     t = k[starts]
     keep = a != 0
     return t[keep].astype(np.float32), np.cumsum(a[keep], dtype=np.int64)
+
+
+def quantize_f32(img: np.ndarray, lo: float, hi: float, bins: int) -> np.ndarray:
+    """The value transform of Sec. 3 ("Other Ranges of Gray Values": shift,
+    scale, round into {0..m-1}), in the reading used here:
+
+        q(v) = clamp(floor((v - lo) * s), 0, bins - 1),  s = bins / (hi - lo),
+
+    every operation in float32 with round-to-nearest: hi - lo, then s, then
+    v - lo, then the product; floor and clamp are exact. Values below lo go to
+    0, values at or above hi to bins - 1. q is non-decreasing in v, so by the
+    paper's remark the integer curve of q(f) is the float curve read at the
+    largest value of each bin. NaN / +-inf and lo >= hi are rejected.
+    Pinned in tests/test_oracle_pins.py (hand-computed codes, identity
+    scaling, the transform relation against `ecc_pairs_float`)."""
+    x = np.asarray(img, dtype=np.float32)
+    if not np.all(np.isfinite(x)):
+        raise ValueError("NaN or infinite value")
+    lo32, hi32 = np.float32(lo), np.float32(hi)
+    if not (np.isfinite(lo32) and np.isfinite(hi32) and lo32 < hi32):
+        raise ValueError("need finite lo < hi")
+    if not 1 <= bins <= 65536:
+        raise ValueError("bins must be in 1..65536")
+    span = np.float32(hi32 - lo32)
+    scale = np.float32(np.float32(bins) / span)
+    d = (x - lo32).astype(np.float32)
+    p = (d * scale).astype(np.float32)
+    code = np.floor(p.astype(np.float64))
+    return np.clip(code, 0, bins - 1).astype(np.int64)
+
+
+def ecc_quantized(img: np.ndarray, lo: float, hi: float, bins: int,
+                  convention: str = "V") -> np.ndarray:
+    """Curve chi({q(f) <= k}), k = 0..bins-1, of the transformed image."""
+    return ecc_int(quantize_f32(img, lo, hi, bins), bins, convention)
 
 
 def cell_counts(img_shape, convention: str = "V"):

@@ -269,6 +269,95 @@ def test_rejects_bad_values():
 
 
 # --------------------------------------------------------------------------
+# the value transform (Sec. 3, "Other Ranges of Gray Values")
+# --------------------------------------------------------------------------
+
+def test_quantize_hand_codes():
+    """q(v) = clamp(floor((v - lo) * bins / (hi - lo)), 0, bins - 1) on values
+    where every float32 step is exact: lo = -1, hi = 1, bins = 4 (scale 2)."""
+    v = np.array([-3.0, -1.0, -0.75, -0.5, -0.25, 0.0, 0.25, 0.5, 0.75, 0.999, 1.0, 7.5],
+                 np.float32)
+    want = [0, 0, 0, 1, 1, 2, 2, 3, 3, 3, 3, 3]
+    assert oracle.quantize_f32(v, -1.0, 1.0, 4).tolist() == want
+
+
+def test_quantize_identity_scale():
+    """lo = 0, hi = bins (scale 1): integer-valued floats map to themselves,
+    so the transformed curve is the integer curve of the same values."""
+    rng = np.random.default_rng(21)
+    img = rng.integers(0, 50, size=(5, 6, 7))
+    f = img.astype(np.float32)
+    assert oracle.quantize_f32(f, 0.0, 50.0, 50).tolist() == img.tolist()
+    for conv in CONVS:
+        assert (oracle.ecc_quantized(f, 0.0, 50.0, 50, conv).tolist() ==
+                oracle.ecc_int(img, 50, conv).tolist())
+
+
+@pytest.mark.parametrize("conv", CONVS)
+@pytest.mark.parametrize("shape", [(23,), (9, 8), (5, 4, 6), (3, 4, 3, 3)])
+def test_quantized_curve_is_float_curve_at_bin_tops(conv, shape):
+    """Sec. 3: the integer algorithm on transformed values gives the float
+    curve with its domain transformed. q is non-decreasing, so {q(f) <= k} =
+    {f <= m_k} with m_k the largest image value whose code is <= k: the
+    transformed curve at k is the float curve (the independent float-keyed
+    enumeration) read at m_k, and 0 where no value has a code <= k."""
+    rng = np.random.default_rng(31 + len(shape))
+    img = rng.normal(size=shape).astype(np.float32)
+    lo, hi, bins = -1.3, 1.1, 37
+    qc = oracle.ecc_quantized(img, lo, hi, bins, conv)
+    t, chi = oracle.ecc_pairs_float(img, conv)
+    codes = oracle.quantize_f32(img, lo, hi, bins).ravel()
+    vals = img.ravel()
+    for k in range(bins):
+        sel = vals[codes <= k]
+        want = 0
+        if sel.size:
+            i = np.searchsorted(t, sel.max(), side="right") - 1
+            want = int(chi[i]) if i >= 0 else 0
+        assert qc[k] == want
+
+
+def test_quantize_monotone_and_rejects():
+    v = np.sort(np.random.default_rng(5).normal(size=10000).astype(np.float32) * 3)
+    q = oracle.quantize_f32(v, -2.0, 2.5, 1000)
+    assert np.all(np.diff(q) >= 0) and q.min() == 0 and q.max() == 999
+    with pytest.raises(ValueError):
+        oracle.quantize_f32(np.array([np.nan], np.float32), 0.0, 1.0, 4)
+    with pytest.raises(ValueError):
+        oracle.quantize_f32(np.zeros(3, np.float32), 1.0, 1.0, 4)
+    with pytest.raises(ValueError):
+        oracle.quantize_f32(np.zeros(3, np.float32), 0.0, 1.0, 70000)
+
+
+def test_quantize_float32_rounding():
+    """The code is decided in float32: 0.7f = 0.69999998807..., times 10 is
+    6.9999998807... exactly, which rounds to 7.0 in float32 (the nearest
+    float32 values are 6.99999952... and 7.0), so the code is 7, not the 6 of
+    exact arithmetic."""
+    v = np.array([0.7, 0.3, 0.1], np.float32)
+    assert oracle.quantize_f32(v, 0.0, 1.0, 10).tolist() == [7, 3, 1]
+
+
+def _quant_pins_pass() -> bool:
+    try:
+        test_quantize_hand_codes()
+        test_quantize_identity_scale()
+        test_quantize_float32_rounding()
+    except AssertionError:
+        return False
+    return True
+
+
+@pytest.mark.parametrize("name", ["ceil instead of floor", "no clamp", "no float32 rounding"])
+def test_planted_quantizer_mistake_is_caught(name, monkeypatch):
+    swap = {"ceil instead of floor": {"floor": np.ceil},
+            "no clamp": {"clip": lambda a, lo, hi: a},
+            "no float32 rounding": {"float32": np.float64}}[name]
+    monkeypatch.setattr(ecc_oracle, "np", _NumpyWith(**swap))
+    assert not _quant_pins_pass(), f"no pin catches: {name}"
+
+
+# --------------------------------------------------------------------------
 # planted mistakes: each must be caught by at least one pin above
 # --------------------------------------------------------------------------
 

@@ -138,6 +138,20 @@ int ecc_compute_device(ecc_handle* h, const void* d_image, const int64_t* dims,
                        int ndim, ecc_dtype dtype, int64_t bins,
                        int64_t* d_curve, void* stream);
 
+/* ECC of a float32 image through the value transform of Sec. 3 ("Other
+ * Ranges of Gray Values": shift, scale and round the values into 0..m-1, then
+ * run the integer algorithm): code(v) = clamp(floor((v - lo) * s), 0, bins-1)
+ * with s = bins / (hi - lo), each step a float32 operation rounded to nearest
+ * (hi - lo, s, v - lo, the product). curve[k] = chi of {voxels with code <= k},
+ * which is the exact float curve read at the largest image value of code k.
+ * image: host or device float32, C order, 1-4D. bins: 1..65536 (codes are
+ * uint8 up to 256 bins, else uint16). Blocks until *out holds the curve
+ * (owned by the library). Errors: ECC_ERR_ARG (lo >= hi, non-finite lo / hi,
+ * bins out of range), ECC_ERR_VALUE (NaN or Inf in the image), ECC_ERR_OOM,
+ * ECC_ERR_CUDA. */
+int ecc_compute_quantized(ecc_handle* h, const float* image, const int64_t* dims, int ndim,
+                          float lo, float hi, int64_t bins, ecc_result* out);
+
 /* Synchronises the handle's device work and returns ECC_ERR_VALUE if any
  * ecc_compute_device call since the last ecc_device_status saw a value
  * >= bins, else ECC_OK (or ECC_ERR_CUDA). Clears the flag. */
@@ -165,6 +179,19 @@ int ecc_stream_finish(ecc_stream* s, ecc_result* out);
 
 /* Drops a stream without a result. */
 void ecc_stream_abort(ecc_stream* s);
+
+/* Out-of-core streaming from a file (Sec. 3, "Streaming", where chunks are
+ * read from disk; Sec. 5 runs terabyte images this way): the image is stored
+ * raw at byte `offset` of the file at `path` (C order, native byte order, no
+ * padding, dims and integer dtype as for ecc_stream_begin). A reader thread
+ * fills two pinned slab buffers of cfg->slab_depth planes with pread while
+ * the other is pushed through the device ring. Blocks until *out holds the
+ * curve (owned by the library). Errors: ECC_ERR_ARG (file missing, shorter
+ * than offset + image bytes, or a read failed), ECC_ERR_DTYPE, ECC_ERR_VALUE,
+ * ECC_ERR_OOM, ECC_ERR_TIMEOUT (a slab read took over 10 minutes),
+ * ECC_ERR_CUDA. */
+int ecc_stream_file(ecc_handle* h, const char* path, int64_t offset, const int64_t* dims,
+                    int ndim, ecc_dtype dtype, ecc_result* out);
 
 /* Batched computation: all images of the batch in one persistent launch
  * whose blocks take (image, tile) items from a work list. Images of any

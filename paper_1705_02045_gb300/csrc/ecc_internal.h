@@ -55,6 +55,13 @@ struct LocalArgs {
 // kernel launches.
 cudaError_t launch_local(const LocalArgs& a, int num_sms, int64_t* launches);
 
+// Codes of the value transform (k_quant.cu): out[i] = clamp(floor((in[i] - lo)
+// * scale), 0, bins - 1) as uint8 (code_bytes 1) or uint16 (2), float32
+// round-to-nearest steps; NaN / inf set kErrValue in *err.
+cudaError_t launch_quantize(const float* in, void* out, int code_bytes, int64_t n, float lo,
+                            float scale, int64_t bins, int* err, int num_sms, cudaStream_t stream,
+                            int64_t* launches);
+
 // curve[t] = sum_{s <= t} vcec[s], t < bins (one block).
 cudaError_t launch_scan(const long long* vcec, long long* curve, int64_t bins,
                         cudaStream_t stream, int64_t* launches);

@@ -3,6 +3,8 @@
 // point catches and converts to a status code.
 #include "engine.h"
 
+#include <cmath>
+
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -399,7 +401,7 @@ void ecc_destroy(ecc_handle* h) {
   if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
   for (DevBuf* b : {&h->img, &h->vcec, &h->curve, &h->errw, &h->pairs, &h->pair_count, &h->tmp,
                     &h->out_keys, &h->out_chi, &h->out_count, &h->batch_desc, &h->batch_items,
-                    &h->batch_vcec, &h->batch_curve})
+                    &h->batch_vcec, &h->batch_curve, &h->codes})
     b->release();
   for (auto& pr : h->prof_events) {
     cudaEventDestroy(pr.first);
@@ -535,6 +537,83 @@ int ecc_compute_device(ecc_handle* h, const void* d_image, const int64_t* dims, 
     if ((rc = stage_image(h, d_image, true, s, dtype, bins, st, &d_img, &pitch))) return rc;
     return enqueue_int(h, d_img, pitch, s, dtype, bins, h->vcec.as<long long>(),
                        reinterpret_cast<long long*>(d_curve), st);
+  } catch (...) {
+    return set_err(h, ECC_ERR_CUDA, "internal error");
+  }
+}
+
+int ecc_compute_quantized(ecc_handle* h, const float* image, const int64_t* dims, int ndim,
+                          float lo, float hi, int64_t bins, ecc_result* out) {
+  if (!h) return ECC_ERR_ARG;
+  try {
+    std::lock_guard<std::mutex> lk(h->api_mu);
+    h->err.clear();
+    if (!out) return set_err(h, ECC_ERR_ARG, "out is NULL");
+    std::memset(out, 0, sizeof *out);
+    out->owned = 1;
+    Shape s;
+    int rc = validate_shape(h, dims, ndim, &s);
+    if (rc) return rc;
+    if (!std::isfinite(lo) || !std::isfinite(hi) || !(lo < hi))
+      return set_err(h, ECC_ERR_ARG, "need finite lo < hi");
+    if (bins < 1 || bins > 65536) return set_err(h, ECC_ERR_ARG, "bins must be in 1..65536");
+    if (s.voxels > 0 && !image) return set_err(h, ECC_ERR_ARG, "image is NULL");
+    // the transform's constants, float32 round-to-nearest like the codes
+    const float span = hi - lo;
+    const float scale = (float)bins / span;
+    if (!std::isfinite(scale)) return set_err(h, ECC_ERR_ARG, "hi - lo too small");
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e) return cuda_err(h, e, "set device");
+    const int code_dtype = bins <= 256 ? ECC_U8 : ECC_U16;
+    const size_t code_bytes = dtype_bytes(code_dtype);
+    if ((e = h->vcec.ensure(sizeof(long long) * bins)) ||
+        (e = h->curve.ensure(sizeof(long long) * bins)) ||
+        (e = h->codes.ensure(code_bytes * (size_t)std::max<int64_t>(s.voxels, 1))))
+      return cuda_err(h, e, "buffers");
+    if ((e = cudaMemsetAsync(h->errw.p, 0, sizeof(int), h->stream))) return cuda_err(h, e, "memset");
+    const float* d_in = image;
+    if (s.voxels > 0 && !is_device_ptr(h, image)) {
+      if ((e = h->img.ensure(sizeof(float) * s.voxels))) return cuda_err(h, e, "image buffer");
+      if ((e = cudaMemcpyAsync(h->img.p, image, sizeof(float) * s.voxels,
+                               cudaMemcpyHostToDevice, h->stream)))
+        return cuda_err(h, e, "copy image");
+      d_in = h->img.as<float>();
+    }
+    int64_t cnt = 0;
+    e = launch_quantize(d_in, h->codes.p, (int)code_bytes, s.voxels, lo, scale, bins,
+                        h->errw.as<int>(), h->num_sms, h->stream, &cnt);
+    h->launches += cnt;
+    if (e) return cuda_err(h, e, "quantize kernel");
+    rc = enqueue_int(h, h->codes.p, 0, s, code_dtype, bins, h->vcec.as<long long>(),
+                     h->curve.as<long long>(), h->stream);
+    if (rc) return rc;
+    out->bins = bins;
+    out->curve = static_cast<int64_t*>(std::malloc(sizeof(int64_t) * bins));
+    if (!out->curve) return set_err(h, ECC_ERR_OOM, "host curve");
+    if ((size_t)bins > h->h_curve_cap) {
+      if (h->h_curve) cudaFreeHost(h->h_curve);
+      h->h_curve = nullptr;
+      h->h_curve_cap = 0;
+      if ((e = cudaMallocHost(&h->h_curve, sizeof(int64_t) * bins))) {
+        ecc_result_free(out);
+        return cuda_err(h, e, "pinned curve");
+      }
+      h->h_curve_cap = (size_t)bins;
+    }
+    if ((e = cudaMemcpyAsync(h->h_curve, h->curve.p, sizeof(int64_t) * bins,
+                             cudaMemcpyDeviceToHost, h->stream))) {
+      ecc_result_free(out);
+      return cuda_err(h, e, "copy curve");
+    }
+    int word = 0;
+    if ((rc = read_err_word(h, h->stream, &word)) || (rc = err_word_status(h, word))) {
+      ecc_result_free(out);
+      return rc;
+    }
+    std::memcpy(out->curve, h->h_curve, sizeof(int64_t) * bins);
+    return ECC_OK;
+  } catch (const std::bad_alloc&) {
+    return set_err(h, ECC_ERR_OOM, "host allocation failed");
   } catch (...) {
     return set_err(h, ECC_ERR_CUDA, "internal error");
   }

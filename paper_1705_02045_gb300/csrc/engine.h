@@ -89,6 +89,7 @@ struct ecc_handle {
   int64_t launch_tmp = 0;
 
   ecc::DevBuf img, vcec, curve, errw, pairs, pair_count, tmp, out_keys, out_chi, out_count;
+  ecc::DevBuf codes;                    // value-transform codes (ecc_compute_quantized)
   ecc::DevBuf batch_desc, batch_items, batch_vcec, batch_curve;
   int* h_err = nullptr;                 // pinned scalar for error readback
   int64_t* h_curve = nullptr;           // pinned staging of integer curves

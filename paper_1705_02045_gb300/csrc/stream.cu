@@ -13,8 +13,19 @@
 // the copy stream, no host blocking).
 #include "engine.h"
 
+#include <fcntl.h>
+#include <sys/stat.h>
+#include <unistd.h>
+
+#include <atomic>
+#include <cerrno>
+#include <chrono>
+#include <condition_variable>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <thread>
+#include <vector>
 
 namespace ecc {
 
@@ -326,6 +337,140 @@ void ecc_stream_abort(ecc_stream* st) {
     release(st);
   } catch (...) {
   }
+}
+
+// Out-of-core streaming from a file (Sec. 3, "Streaming": chunks read from
+// disk; the terabyte images of Sec. 5 are processed this way). A reader
+// thread fills two pinned slab buffers with pread (each slab split over up to
+// kReadThreads parallel readers) while the caller's thread pushes the other
+// one through the device ring, so disk reads, host-to-device copies and
+// kernels overlap.
+constexpr int kReadThreads = 8;
+
+int ecc_stream_file(ecc_handle* h, const char* path, int64_t offset, const int64_t* dims,
+                    int ndim, ecc_dtype dtype, ecc_result* out) {
+  if (!h) return ECC_ERR_ARG;
+  if (!out || !path || offset < 0) return set_err(h, ECC_ERR_ARG, "bad path, offset or out");
+  std::memset(out, 0, sizeof *out);
+  ecc_stream* st = nullptr;
+  int rc = ecc_stream_begin(h, dims, ndim, dtype, &st);
+  if (rc) return rc;
+  const int64_t nz = st->s.n[0];
+  const size_t plane = st->src_row * st->rows_per_plane;
+  const int fd = ::open(path, O_RDONLY);
+  if (fd < 0) {
+    ecc_stream_abort(st);
+    return set_err(h, ECC_ERR_ARG, "cannot open %s: %s", path, std::strerror(errno));
+  }
+  struct stat sb;
+  if (::fstat(fd, &sb) != 0 ||
+      (uint64_t)sb.st_size < (uint64_t)offset + (uint64_t)plane * (uint64_t)nz) {
+    ::close(fd);
+    ecc_stream_abort(st);
+    return set_err(h, ECC_ERR_ARG, "%s is shorter than offset + image bytes", path);
+  }
+#ifdef POSIX_FADV_SEQUENTIAL
+  posix_fadvise(fd, 0, 0, POSIX_FADV_SEQUENTIAL);
+#endif
+  const int64_t depth = std::max<int64_t>(1, std::min<int64_t>(st->depth, nz));
+  void* buf[2] = {nullptr, nullptr};
+  if (plane > 0 && nz > 0) {
+    for (int i = 0; i < 2; ++i) {
+      cudaError_t e = cudaHostAlloc(&buf[i], plane * (size_t)depth, cudaHostAllocDefault);
+      if (e) {
+        cudaGetLastError();
+        for (int j = 0; j < 2; ++j)
+          if (buf[j]) cudaFreeHost(buf[j]);
+        ::close(fd);
+        ecc_stream_abort(st);
+        return set_err(h, ECC_ERR_OOM, "pinned slab buffers");
+      }
+    }
+  }
+  // slab k lives in buf[k & 1]; full[i] = slab index held by buffer i, or -1
+  std::mutex mu;
+  std::condition_variable cv;
+  int64_t full[2] = {-1, -1};
+  bool stop = false;
+  int read_err = 0;
+  const int64_t slabs = plane > 0 ? (nz + depth - 1) / depth : 0;
+  std::thread reader([&] {
+    for (int64_t k = 0; k < slabs; ++k) {
+      const int i = (int)(k & 1);
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [&] { return stop || full[i] < 0; });
+        if (stop) return;
+      }
+      const int64_t z0 = k * depth, n = std::min(depth, nz - z0);
+      const size_t want = plane * (size_t)n;
+      char* dst = static_cast<char*>(buf[i]);
+      const off_t base = (off_t)(offset + (int64_t)plane * z0);
+      // the slab in parts of >= 32 MiB read by parallel preads (one thread
+      // copying out of the page cache is far slower than the ring)
+      const size_t part = std::max<size_t>(size_t(32) << 20, (want + kReadThreads - 1) / kReadThreads);
+      std::atomic<int> err{0};
+      auto read_range = [&](size_t lo, size_t hi) {
+        while (lo < hi && !err.load()) {
+          const ssize_t r = ::pread(fd, dst + lo, hi - lo, base + (off_t)lo);
+          if (r < 0 && errno == EINTR) continue;
+          if (r <= 0) {
+            err = r < 0 ? errno : EIO;
+            return;
+          }
+          lo += (size_t)r;
+        }
+      };
+      std::vector<std::thread> parts;
+      for (size_t lo = part; lo < want; lo += part)
+        parts.emplace_back(read_range, lo, std::min(want, lo + part));
+      read_range(0, std::min(want, part));
+      for (std::thread& t : parts) t.join();
+      std::lock_guard<std::mutex> lk(mu);
+      if (err.load()) {
+        read_err = err.load();
+      } else {
+        full[i] = k;
+      }
+      cv.notify_all();
+      if (read_err) return;
+    }
+  });
+  rc = ECC_OK;
+  for (int64_t k = 0; k < slabs && rc == ECC_OK; ++k) {
+    const int i = (int)(k & 1);
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      // a read of one slab: bounded at 10 minutes
+      if (!cv.wait_for(lk, std::chrono::minutes(10), [&] { return full[i] == k || read_err; }))
+        rc = set_err(h, ECC_ERR_TIMEOUT, "reading slab %lld timed out", (long long)k);
+      else if (read_err)
+        rc = set_err(h, ECC_ERR_ARG, "reading %s failed: %s", path, std::strerror(read_err));
+    }
+    if (rc) break;
+    const int64_t z0 = k * depth, n = std::min(depth, nz - z0);
+    rc = ecc_stream_push_slab(st, buf[i], z0, n);
+    std::lock_guard<std::mutex> lk(mu);
+    full[i] = -1;  // the push returned: the buffer may be refilled
+    cv.notify_all();
+  }
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    stop = true;
+    cv.notify_all();
+  }
+  reader.join();
+  ::close(fd);
+  if (rc == ECC_OK) {
+    rc = ecc_stream_finish(st, out);
+  } else {
+    const std::string msg = h->err;
+    ecc_stream_abort(st);
+    h->err = msg;
+  }
+  for (int j = 0; j < 2; ++j)
+    if (buf[j]) cudaFreeHost(buf[j]);
+  return rc;
 }
 
 }  // extern "C"

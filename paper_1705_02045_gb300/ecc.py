@@ -59,10 +59,14 @@ _SIGNATURES = {
     "ecc_compute": (C.c_int, [_P, _P, _I64P, C.c_int, C.c_int, C.POINTER(ecc_result)]),
     "ecc_compute_device": (C.c_int, [_P, _P, _I64P, C.c_int, C.c_int, C.c_int64, _P, _P]),
     "ecc_device_status": (C.c_int, [_P]),
+    "ecc_compute_quantized": (C.c_int, [_P, _P, _I64P, C.c_int, C.c_float, C.c_float, C.c_int64,
+                                        C.POINTER(ecc_result)]),
     "ecc_stream_begin": (C.c_int, [_P, _I64P, C.c_int, C.c_int, C.POINTER(_P)]),
     "ecc_stream_push_slab": (C.c_int, [_P, _P, C.c_int64, C.c_int64]),
     "ecc_stream_finish": (C.c_int, [_P, C.POINTER(ecc_result)]),
     "ecc_stream_abort": (None, [_P]),
+    "ecc_stream_file": (C.c_int, [_P, C.c_char_p, C.c_int64, _I64P, C.c_int, C.c_int,
+                                  C.POINTER(ecc_result)]),
     "ecc_compute_batch": (C.c_int, [_P, C.c_int, C.POINTER(ecc_image), C.POINTER(ecc_result)]),
     "ecc_submit": (C.c_int, [_P, _P, _I64P, C.c_int, C.c_int, C.POINTER(C.c_uint64)]),
     "ecc_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(ecc_result), C.c_int64]),
@@ -188,6 +192,24 @@ def ecc_compute(h, image):
         del keep
 
 
+def ecc_compute_quantized(h, image, lo: float, hi: float, bins: int):
+    """Curve (int64[bins]) of a float32 image (numpy array or torch tensor,
+    host or CUDA) through the value transform code = clamp(floor((v - lo) *
+    bins / (hi - lo)), 0, bins - 1)."""
+    if _dtype_code(image.dtype) != ECC_F32:
+        raise TypeError("ecc_compute_quantized takes a float32 image")
+    lib = load()
+    ptr, keep = _data_ptr(image)
+    r = ecc_result()
+    _check(h, lib.ecc_compute_quantized(h, ptr, _dims(image.shape), len(image.shape),
+                                        C.c_float(lo), C.c_float(hi), int(bins), C.byref(r)))
+    try:
+        return _result_to_numpy(r)
+    finally:
+        lib.ecc_result_free(C.byref(r))
+        del keep
+
+
 def ecc_compute_device(h, d_image, bins: int, d_curve, stream=None) -> None:
     """Enqueues an integer CUDA-tensor image; writes the int64 CUDA tensor
     ``d_curve[bins]``; ``stream`` is a torch.cuda.Stream or None."""
@@ -228,6 +250,19 @@ def ecc_stream_finish(h, s):
 
 def ecc_stream_abort(s) -> None:
     load().ecc_stream_abort(s)
+
+
+def ecc_stream_file(h, path, shape, dtype, offset: int = 0):
+    """Curve of a raw C-order integer image stored at byte `offset` of the
+    file `path`, streamed slab by slab."""
+    lib = load()
+    r = ecc_result()
+    _check(h, lib.ecc_stream_file(h, os.fsencode(path), int(offset), _dims(shape), len(shape),
+                                  _dtype_code(dtype), C.byref(r)))
+    try:
+        return _result_to_numpy(r)
+    finally:
+        lib.ecc_result_free(C.byref(r))
 
 
 def ecc_compute_batch(h, images, bins=None):

@@ -321,3 +321,71 @@ def test_serve_streamed_request_errors(lib):
         assert ei.value.status == ecc.ECC_ERR_OOM
     finally:
         ecc.ecc_destroy(h)
+
+
+# ---- out-of-core from a file ---------------------------------------------------
+
+@pytest.mark.parametrize("dtype,bins", [(np.uint8, 256), (np.uint16, 16384)])
+def test_stream_file_matches_oracle(lib, tmp_path, dtype, bins):
+    """A raw image after a 123-byte header, streamed in slabs of 4 planes
+    through a small ring (many slabs, both pinned buffers in turn)."""
+    if dtype == np.uint8:
+        img = synth.smooth_u8((37, 29, 45), 2.0, S + 60)
+    else:
+        img = synth.two_phase_u16((37, 29, 45), 1.5, S + 61)
+    path = tmp_path / "vol.raw"
+    with open(path, "wb") as f:
+        f.write(b"h" * 123)
+        f.write(np.ascontiguousarray(img).tobytes())
+    h = ecc.ecc_create(device=0, bins=bins, slab_depth=4, ring_bytes=1 << 20)
+    try:
+        got = ecc.ecc_stream_file(h, path, img.shape, img.dtype, offset=123)
+        whole = ecc.ecc_compute(h, img)
+    finally:
+        ecc.ecc_destroy(h)
+    want = oracle.ecc_int(img, bins, "V")
+    assert np.array_equal(got, want) and np.array_equal(whole, want)
+
+
+@pytest.mark.parametrize("shape", [(300,), (40, 70), (1, 5, 6)], ids=str)
+def test_stream_file_1d_2d_single_plane(lib, tmp_path, shape):
+    img = synth.uniform_u8(shape, S + 62 + len(shape))
+    path = tmp_path / "img.raw"
+    img.tofile(path)
+    h = ecc.ecc_create(device=0, slab_depth=3)
+    try:
+        got = ecc.ecc_stream_file(h, path, img.shape, img.dtype)
+    finally:
+        ecc.ecc_destroy(h)
+    assert np.array_equal(got, oracle.ecc_int(img, 256, "V"))
+
+
+def test_stream_file_errors(lib, tmp_path):
+    img = synth.uniform_u8((6, 7, 8), S + 63)
+    path = tmp_path / "short.raw"
+    img[:5].tofile(path)  # one plane short
+    h = ecc.ecc_create(device=0, slab_depth=2)
+    try:
+        with pytest.raises(ecc.EccError) as ei:
+            ecc.ecc_stream_file(h, path, img.shape, img.dtype)
+        assert ei.value.status == ecc.ECC_ERR_ARG
+        with pytest.raises(ecc.EccError) as ei:
+            ecc.ecc_stream_file(h, tmp_path / "missing.raw", img.shape, img.dtype)
+        assert ei.value.status == ecc.ECC_ERR_ARG
+        bad = img.astype(np.uint16)
+        bad[3, 2, 1] = 300
+        p2 = tmp_path / "bad.raw"
+        bad.tofile(p2)
+        h2 = ecc.ecc_create(device=0, bins=256, slab_depth=2)
+        try:
+            with pytest.raises(ecc.EccError) as ei:
+                ecc.ecc_stream_file(h2, p2, bad.shape, bad.dtype)
+            assert ei.value.status == ecc.ECC_ERR_VALUE
+        finally:
+            ecc.ecc_destroy(h2)
+        # the handle still works
+        img.tofile(path)
+        assert np.array_equal(ecc.ecc_stream_file(h, path, img.shape, img.dtype),
+                              oracle.ecc_int(img, 256, "V"))
+    finally:
+        ecc.ecc_destroy(h)

@@ -5,6 +5,7 @@
 
 #include <cmath>
 
+#include <algorithm>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -130,8 +131,14 @@ int stage_image(ecc_handle* h, const void* image, bool on_device, const Shape& s
   return ECC_OK;
 }
 
+// Host images of at least this many bytes are uploaded in plane chunks that
+// overlap with the computation (ecc_compute); at most kUploadChunksMax chunks.
+constexpr size_t kChunkedUploadBytes = size_t(16) << 20;
+constexpr int64_t kUploadChunksMax = 16;
+
 int enqueue_int(ecc_handle* h, const void* d_img, int64_t row_pitch, const Shape& s, int dtype,
-                int64_t bins, long long* d_vcec, long long* d_curve, cudaStream_t stream) {
+                int64_t bins, long long* d_vcec, long long* d_curve, cudaStream_t stream,
+                const int64_t* chunk_end, const cudaEvent_t* chunk_ev, int n_chunks) {
   cudaError_t e = cudaMemsetAsync(d_vcec, 0, sizeof(long long) * bins, stream);
   if (e != cudaSuccess) return cuda_err(h, e, "memset vcec");
   if (s.voxels > 0) {
@@ -161,6 +168,9 @@ int enqueue_int(ecc_handle* h, const void* d_img, int64_t row_pitch, const Shape
       const std::string k = Tuner::key(t);
       TuneChoice c;
       if (!h->tuner->lookup(k, &c)) {
+        // the candidates read the whole first launch's planes: all chunks first
+        if (n_chunks > 0 && (e = cudaStreamWaitEvent(stream, chunk_ev[n_chunks - 1], 0)))
+          return cuda_err(h, e, "wait upload");
         int rc = tune_bits(h, t, &c);
         if (rc) return rc;
         if (c.warps > 0) h->tuner->store(k, c);
@@ -177,13 +187,20 @@ int enqueue_int(ecc_handle* h, const void* d_img, int64_t row_pitch, const Shape
           (e = cudaEventRecord(ev0, stream)))
         return cuda_err(h, e, "profiling event");
     }
-    for (int64_t w = 0; w < a.n[0]; w += step) {
-      a.w_lo = w;
-      a.w_hi = std::min(a.n[0], w + step);
-      int64_t cnt = 0;
-      e = launch_local(a, h->num_sms, &cnt);
-      h->launches += cnt;
-      if (e != cudaSuccess) return cuda_err(h, e, "contribution kernel");
+    const int K = n_chunks > 0 ? n_chunks : 1;
+    for (int k = 0; k < K; ++k) {
+      const int64_t lo = n_chunks > 0 && k > 0 ? chunk_end[k - 1] : 0;
+      const int64_t hi = n_chunks > 0 ? chunk_end[k] : a.n[0];
+      if (n_chunks > 0 && (e = cudaStreamWaitEvent(stream, chunk_ev[std::min(k + 1, K - 1)], 0)))
+        return cuda_err(h, e, "wait upload");
+      for (int64_t w = lo; w < hi; w += step) {
+        a.w_lo = w;
+        a.w_hi = std::min(hi, w + step);
+        int64_t cnt = 0;
+        e = launch_local(a, h->num_sms, &cnt);
+        h->launches += cnt;
+        if (e != cudaSuccess) return cuda_err(h, e, "contribution kernel");
+      }
     }
     if (h->prof_on) {
       if ((e = cudaEventRecord(ev1, stream))) return cuda_err(h, e, "profiling event");
@@ -410,6 +427,8 @@ void ecc_destroy(ecc_handle* h) {
   delete h->tuner;
   if (h->h_err) cudaFreeHost(h->h_err);
   if (h->h_curve) cudaFreeHost(h->h_curve);
+  for (cudaEvent_t ev : h->up_ev) cudaEventDestroy(ev);
+  if (h->up_free) cudaEventDestroy(h->up_free);
   if (h->stream) cudaStreamDestroy(h->stream);
   if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   delete h;
@@ -479,9 +498,45 @@ int ecc_compute(ecc_handle* h, const void* image, const int64_t* dims, int ndim,
       return cuda_err(h, e, "vcec buffers");
     const void* d_img = nullptr;
     int64_t pitch = 0;
-    if ((rc = stage_image(h, image, on_dev, s, dtype, bins, h->stream, &d_img, &pitch))) return rc;
-    rc = enqueue_int(h, d_img, pitch, s, dtype, bins, h->vcec.as<long long>(),
-                     h->curve.as<long long>(), h->stream);
+    const size_t bytes = eb * (size_t)s.voxels;
+    if (!on_dev && bytes >= kChunkedUploadBytes && s.n[0] >= 2) {
+      // large host image: upload in plane chunks on the copy stream and start
+      // each chunk's kernels as soon as it (and the next chunk's first plane)
+      // has arrived, so the copy and the computation overlap
+      if ((e = h->img.ensure(bytes))) return cuda_err(h, e, "image buffer");
+      const int64_t plane = (int64_t)(bytes / (size_t)s.n[0]);
+      const int K = (int)std::min<int64_t>(
+          {s.n[0], kUploadChunksMax, std::max<int64_t>(2, (int64_t)(bytes / kChunkedUploadBytes) * 4)});
+      while ((int)h->up_ev.size() < K) {
+        cudaEvent_t ev;
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming))) return cuda_err(h, e, "event");
+        h->up_ev.push_back(ev);
+      }
+      if (!h->up_free && (e = cudaEventCreateWithFlags(&h->up_free, cudaEventDisableTiming)))
+        return cuda_err(h, e, "event");
+      // the buffer's earlier readers (kernels on the compute stream) first
+      if ((e = cudaEventRecord(h->up_free, h->stream)) ||
+          (e = cudaStreamWaitEvent(h->copy_stream, h->up_free, 0)))
+        return cuda_err(h, e, "order upload");
+      std::vector<int64_t> ends(K);
+      for (int k = 0; k < K; ++k) {
+        const int64_t z0 = s.n[0] * k / K, z1 = s.n[0] * (k + 1) / K;
+        ends[k] = z1;
+        char* dst = static_cast<char*>(h->img.p) + (size_t)(z0 * plane);
+        const char* src = static_cast<const char*>(image) + (size_t)(z0 * plane);
+        if ((e = cudaMemcpyAsync(dst, src, (size_t)((z1 - z0) * plane), cudaMemcpyHostToDevice,
+                                 h->copy_stream)) ||
+            (e = cudaEventRecord(h->up_ev[k], h->copy_stream)))
+          return cuda_err(h, e, "copy image");
+      }
+      rc = enqueue_int(h, h->img.p, 0, s, dtype, bins, h->vcec.as<long long>(),
+                       h->curve.as<long long>(), h->stream, ends.data(), h->up_ev.data(), K);
+    } else {
+      if ((rc = stage_image(h, image, on_dev, s, dtype, bins, h->stream, &d_img, &pitch)))
+        return rc;
+      rc = enqueue_int(h, d_img, pitch, s, dtype, bins, h->vcec.as<long long>(),
+                       h->curve.as<long long>(), h->stream);
+    }
     if (rc) return rc;
     out->bins = bins;
     out->curve = static_cast<int64_t*>(std::malloc(sizeof(int64_t) * bins));

@@ -92,6 +92,8 @@ struct ecc_handle {
   ecc::DevBuf codes;                    // value-transform codes (ecc_compute_quantized)
   ecc::DevBuf batch_desc, batch_items, batch_vcec, batch_curve;
   int* h_err = nullptr;                 // pinned scalar for error readback
+  std::vector<cudaEvent_t> up_ev;       // chunked host-image upload (ecc_compute)
+  cudaEvent_t up_free = nullptr;        // the image buffer's previous readers are done
   int64_t* h_curve = nullptr;           // pinned staging of integer curves
   size_t h_curve_cap = 0;               // entries of h_curve
 
@@ -114,8 +116,14 @@ size_t dtype_bytes(int dtype);
 bool is_device_ptr(const ecc_handle* h, const void* p);
 // Enqueues VCEC accumulation (zeroed first) + contribution kernel + scan of
 // an integer image already on the device.
+// With n_chunks > 0 the image is still arriving in plane chunks: planes
+// [chunk_end[k-1], chunk_end[k]) are on the device once chunk_ev[k] completed,
+// and the contribution launches of a chunk wait for the next chunk's event
+// (its first plane is their upper collar).
 int enqueue_int(ecc_handle* h, const void* d_img, int64_t row_pitch, const Shape& s, int dtype,
-                int64_t bins, long long* d_vcec, long long* d_curve, cudaStream_t stream);
+                int64_t bins, long long* d_vcec, long long* d_curve, cudaStream_t stream,
+                const int64_t* chunk_end = nullptr, const cudaEvent_t* chunk_ev = nullptr,
+                int n_chunks = 0);
 // True when the bit-sliced kernel applies to this shape / dtype / bin count.
 bool bits_eligible(const ecc_handle* h, const Shape& s, int dtype, int64_t bins);
 // Device copy of an image for the contribution kernels: a device image is used

@@ -57,17 +57,34 @@ k_local3(const LocalArgs a, int64_t zc, int64_t tiles_x, int64_t tiles_y, int64_
 }
 
 // ---------------------------------------------------------------------------
-// 4D view (w, z, y, x); tile 32 x 4 x 2 in (x, y, z), marching along w.
+// 4D view (w, z, y, x); tile 128 x 4 x 2 in (x, y, z), marching along w. Each
+// thread owns 4 consecutive voxels in x: the 6 keys of a neighbour row that
+// they need (x - 1 .. x + 4) are one 16-byte and one 8-byte shared-memory
+// load, so the 80 neighbours of a voxel cost 13.5 loads instead of 80. Halo
+// rows hold 130 keys padded to 132 (16-byte aligned rows).
 // ---------------------------------------------------------------------------
+constexpr int k4TX = 128, k4TY = 4, k4TZ = 2, k4VX = 4;
+constexpr int k4PW = 132, k4PH = k4TY + 2, k4PD = k4TZ + 2, k4PL = k4PW * k4PH * k4PD;
+static_assert(k4TX / k4VX * k4TY * k4TZ == kThreads, "one thread per 4 voxels");
+
+__device__ __forceinline__ void load6(const uint32_t* p, uint32_t k[6]) {
+  const uint4 q = *reinterpret_cast<const uint4*>(p);
+  const uint2 r = *reinterpret_cast<const uint2*>(p + 4);
+  k[0] = q.x;
+  k[1] = q.y;
+  k[2] = q.z;
+  k[3] = q.w;
+  k[4] = r.x;
+  k[5] = r.y;
+}
+
 template <typename T, int CONV, int MODE>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
 k_local4(const LocalArgs a, int64_t wc, int64_t tiles_x, int64_t tiles_y, int64_t tiles_z,
          int64_t n_tiles) {
-  constexpr int TX = 32, TY = 4, TZ = 2, PW = TX + 2, PH = TY + 2, PD = TZ + 2;
-  constexpr int PL = PW * PH * PD;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* ring = reinterpret_cast<uint32_t*>(smem);
-  int8_t* g2 = reinterpret_cast<int8_t*>(ring + 4 * PL);
+  int8_t* g2 = reinterpret_cast<int8_t*>(ring + 4 * k4PL);
   Sink s;
   s.bins = a.bins;
   s.vcec = a.vcec;
@@ -77,7 +94,8 @@ k_local4(const LocalArgs a, int64_t wc, int64_t tiles_x, int64_t tiles_y, int64_
   s.pair_count = a.pair_count;
   s.pair_cap = a.pair_cap;
 
-  const int tid = threadIdx.x, tx = tid % TX, ty = (tid / TX) % TY, tz = tid / (TX * TY);
+  const int tid = threadIdx.x, tx = tid % (k4TX / k4VX), ty = (tid / (k4TX / k4VX)) % k4TY,
+            tz = tid / (k4TX / k4VX * k4TY);
   g2[tid] = (int8_t)g2_entry(tid);
   if (MODE == kSmemHist) clear_smem_hist(s);
   __syncthreads();
@@ -85,75 +103,148 @@ k_local4(const LocalArgs a, int64_t wc, int64_t tiles_x, int64_t tiles_y, int64_
   const T* img = static_cast<const T*>(a.img);
   const int64_t nw = a.n[0], nz = a.n[1], ny = a.n[2], nx = a.n[3];
   const int64_t vol = nz * ny * nx;
+  constexpr int kRowKeys = k4TX + 2;
 
   for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     int64_t r = t;
     const int64_t ix = r % tiles_x; r /= tiles_x;
     const int64_t iy = r % tiles_y; r /= tiles_y;
     const int64_t iz = r % tiles_z; r /= tiles_z;
-    const int64_t x0 = ix * TX, y0 = iy * TY, z0 = iz * TZ;
+    const int64_t x0 = ix * k4TX, y0 = iy * k4TY, z0 = iz * k4TZ;
     const int64_t w0 = a.w_lo + r * wc, w1 = min(w0 + wc, a.w_hi);
 
-    auto load_vol = [&](int64_t wp) {
-      uint32_t* dst = ring + (int)(wp & 3) * PL;
-      for (int i = tid; i < PL; i += kThreads) {
-        const int lz = i / (PW * PH), rr = i - lz * PW * PH, ly = rr / PW, lx = rr - ly * PW;
-        const int64_t gz = z0 + lz - 1, gy = y0 + ly - 1, gx = x0 + lx - 1;
-        uint32_t key = kOutside;
-        if (wp >= 0 && wp < nw && gz >= 0 && gz < nz && gy >= 0 && gy < ny && gx >= 0 &&
-            gx < nx) {
-          if (wp >= a.w_mem_lo && wp < a.w_mem_hi)
-            key = load_key(img, (wp - a.w_mem_lo) * vol + (gz * ny + gy) * nx + gx, a.err);
-          else
-            atomicOr(a.err, kErrOverflow);
+    // Halo volume wp: 24 rows of 130 keys. Warp v takes rows v, v + 8, v + 16
+    // (k4PH * k4PD = 24 = 3 * 8 warps), lane l keys l, l + 32, ... of a row.
+    // fetch() issues the global loads into registers; store() writes the keys
+    // to the volume's ring slot, so the loads of volume w + 2 are in flight
+    // while volume w is evaluated.
+    constexpr int kRowsPerWarp = k4PH * k4PD / (kThreads / 32), kKeysPerLane = (kRowKeys + 31) / 32;
+    static_assert(kRowsPerWarp * (kThreads / 32) == k4PH * k4PD, "rows split evenly");
+    const int warp = tid >> 5, lane = tid & 31;
+    // raw values in flight (the key conversion and the NaN / Inf check wait
+    // for store(), so the loads do not stall the evaluation of volume w) and
+    // a bit per value: inside the image and loaded
+    struct Fetched {
+      T v[kRowsPerWarp][kKeysPerLane];
+      uint32_t in;
+    };
+    auto fetch = [&](int64_t wp, Fetched& f) {
+      const bool wok = wp >= 0 && wp < nw;
+      const bool resident = wp >= a.w_mem_lo && wp < a.w_mem_hi;
+      if (wok && !resident && tid == 0) atomicOr(a.err, kErrOverflow);
+      f.in = 0u;
+#pragma unroll
+      for (int i = 0; i < kRowsPerWarp; ++i) {
+        const int row = warp + i * (kThreads / 32);
+        const int lz = row / k4PH, ly = row - lz * k4PH;
+        const int64_t gz = z0 + lz - 1, gy = y0 + ly - 1;
+        const bool rok = wok && resident && gz >= 0 && gz < nz && gy >= 0 && gy < ny;
+        const int64_t base = rok ? (wp - a.w_mem_lo) * vol + (gz * ny + gy) * nx : 0;
+#pragma unroll
+        for (int k = 0; k < kKeysPerLane; ++k) {
+          const int lx = lane + 32 * k;
+          const int64_t gx = x0 + lx - 1;
+          const bool ok = rok && lx < kRowKeys && gx >= 0 && gx < nx;
+          f.v[i][k] = ok ? img[base + gx] : T(0);
+          f.in |= (ok ? 1u : 0u) << (i * kKeysPerLane + k);
         }
-        dst[i] = key;
       }
     };
-
-    load_vol(w0 - 1);
-    load_vol(w0);
-    load_vol(w0 + 1);
+    auto store = [&](int64_t wp, const Fetched& f) {
+      uint32_t* dst = ring + (int)(wp & 3) * k4PL;
+#pragma unroll
+      for (int i = 0; i < kRowsPerWarp; ++i) {
+        const int row = warp + i * (kThreads / 32);
+#pragma unroll
+        for (int k = 0; k < kKeysPerLane; ++k) {
+          const int lx = lane + 32 * k;
+          if (lx >= kRowKeys) continue;
+          uint32_t key = kOutside;
+          if ((f.in >> (i * kKeysPerLane + k)) & 1u) {
+            const T v = f.v[i][k];
+            if (value_bad(v)) atomicOr(a.err, kErrValue);
+            key = value_key(v);
+          }
+          dst[row * k4PW + lx] = key;
+        }
+      }
+    };
+    Fetched kr;
+    fetch(w0 - 1, kr);
+    store(w0 - 1, kr);
+    fetch(w0, kr);
+    store(w0, kr);
+    fetch(w0 + 1, kr);
+    store(w0 + 1, kr);
     __syncthreads();
 
-    const int64_t gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
-    const bool valid = gx < nx && gy < ny && gz < nz;
-    const int c0 = ((tz + 1) * PH + ty + 1) * PW + tx + 1;
+    const int64_t gx0 = x0 + k4VX * tx, gy = y0 + ty, gz = z0 + tz;
+    const bool row_valid = gy < ny && gz < nz;
+    // halo index of x = gx0 - 1 in the centre row
+    const int c0 = ((tz + 1) * k4PH + ty + 1) * k4PW + k4VX * tx;
     for (int64_t w = w0; w < w1; ++w) {
-      if (w + 2 <= w1) load_vol(w + 2);
-      const uint32_t* vm = ring + (int)((w - 1) & 3) * PL;
-      const uint32_t* v0 = ring + (int)(w & 3) * PL;
-      const uint32_t* vp = ring + (int)((w + 1) & 3) * PL;
-      const uint32_t kv = v0[c0];
-      // 26-bit masks of the volumes w-1, w, w+1 (layout of g3_of_mask) and the
-      // straight neighbours along w.
-      uint32_t M0 = 0, Mp = 0, Mm = 0;
+      const bool next = w + 2 <= w1;
+      if (next) fetch(w + 2, kr);
+      const uint32_t* vm = ring + (int)((w - 1) & 3) * k4PL;
+      const uint32_t* v0 = ring + (int)(w & 3) * k4PL;
+      const uint32_t* vp = ring + (int)((w + 1) & 3) * k4PL;
+      uint32_t kc[6];
+      load6(v0 + c0, kc);
+      // 26-bit masks (layout of g3_of_mask) of the volumes w, w+1, w-1 for
+      // the 4 voxels j (key kc[j + 1]), and the straight neighbours along w
+      uint32_t M0[k4VX] = {}, Mp[k4VX] = {}, Mm[k4VX] = {};
 #pragma unroll
       for (int dz = -1; dz <= 1; ++dz)
 #pragma unroll
-        for (int dy = -1; dy <= 1; ++dy)
+        for (int dy = -1; dy <= 1; ++dy) {
+          const int o = c0 + (dz * k4PH + dy) * k4PW;
+          uint32_t r0[6], rp[6], rm[6];
+          load6(v0 + o, r0);
+          load6(vp + o, rp);
+          load6(vm + o, rm);
 #pragma unroll
           for (int dx = -1; dx <= 1; ++dx) {
-            if (dz == 0 && dy == 0 && dx == 0) continue;
-            const int o = c0 + (dz * PH + dy) * PW + dx;
-            const int bit = dz == 0 ? ring_pos(dy, dx)
+            const bool centre = dz == 0 && dy == 0 && dx == 0;
+            const int bit = dz == 0 ? (centre ? 0 : ring_pos(dy, dx))
                             : (dy == 0 && dx == 0) ? (dz > 0 ? 24 : 25)
                             : (dz > 0 ? 8 : 16) + ring_pos(dy, dx);
             const bool fwd = dz > 0 || (dz == 0 && (dy > 0 || (dy == 0 && dx > 0)));
-            M0 |= (fwd ? after<true>(v0[o], kv) : after<false>(v0[o], kv)) << bit;
-            Mp |= after<true>(vp[o], kv) << bit;
-            Mm |= after<false>(vm[o], kv) << bit;
+#pragma unroll
+            for (int j = 0; j < k4VX; ++j) {
+              const uint32_t kv = kc[j + 1];
+              if (centre) continue;
+              M0[j] |= (fwd ? after<true>(r0[j + 1 + dx], kv) : after<false>(r0[j + 1 + dx], kv))
+                       << bit;
+              Mp[j] |= after<true>(rp[j + 1 + dx], kv) << bit;
+              Mm[j] |= after<false>(rm[j + 1 + dx], kv) << bit;
+            }
           }
-      uint32_t bp = after<true>(vp[c0], kv), bm = after<false>(vm[c0], kv);
-      if (CONV == kConvT) {
-        M0 = ~M0 & 0x3FFFFFFu; Mp = ~Mp & 0x3FFFFFFu; Mm = ~Mm & 0x3FFFFFFu;
-        bp ^= 1u; bm ^= 1u;
+        }
+      // straight neighbours along w (same x, y, z)
+      uint32_t kp[6], km[6];
+      load6(vp + c0, kp);
+      load6(vm + c0, km);
+#pragma unroll
+      for (int j = 0; j < k4VX; ++j) {
+        const uint32_t kv = kc[j + 1];
+        uint32_t m0 = M0[j], mp = Mp[j], mm = Mm[j];
+        uint32_t bp = after<true>(kp[j + 1], kv), bm = after<false>(km[j + 1], kv);
+        if (CONV == kConvT) {
+          m0 = ~m0 & 0x3FFFFFFu;
+          mp = ~mp & 0x3FFFFFFu;
+          mm = ~mm & 0x3FFFFFFu;
+          bp ^= 1u;
+          bm ^= 1u;
+        }
+        int g = g3_of_mask(m0, g2);
+        if (bp) g -= g3_of_mask(m0 & mp, g2);
+        if (bm) g -= g3_of_mask(m0 & mm, g2);
+        // (-1)^4 G_4 for V; G_4 of the complement for T
+        deposit<MODE>(row_valid && gx0 + j < nx, kv, g, s);
       }
-      int g = g3_of_mask(M0, g2);
-      if (bp) g -= g3_of_mask(M0 & Mp, g2);
-      if (bm) g -= g3_of_mask(M0 & Mm, g2);
-      const int c = g;  // (-1)^4 G_4 for V; G_4 of the complement for T
-      deposit<MODE>(valid, kv, c, s);
+      // slot (w + 2) & 3 held volume w - 2, which nobody reads after the
+      // previous step's barrier
+      if (next) store(w + 2, kr);
       __syncthreads();
     }
   }
@@ -189,8 +280,7 @@ cudaError_t launch_typed(const LocalArgs& a, int num_sms, int64_t* launches) {
     ++*launches;
     return cudaGetLastError();
   }
-  constexpr int PL = 34 * 6 * 4;
-  const size_t smem = 4 * PL * 4 + 256 + hist_bytes;
+  const size_t smem = 4 * k4PL * 4 + 256 + hist_bytes;
   auto kern = k_local4<T, CONV, MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
@@ -198,8 +288,8 @@ cudaError_t launch_typed(const LocalArgs& a, int num_sms, int64_t* launches) {
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
   if (e != cudaSuccess) return e;
-  const int64_t tiles_x = (a.n[3] + 31) / 32, tiles_y = (a.n[2] + 3) / 4,
-                tiles_z = (a.n[1] + 1) / 2;
+  const int64_t tiles_x = (a.n[3] + k4TX - 1) / k4TX, tiles_y = (a.n[2] + k4TY - 1) / k4TY,
+                tiles_z = (a.n[1] + k4TZ - 1) / k4TZ;
   const int64_t grid_cap = (int64_t)std::max(per_sm, 1) * num_sms;
   int64_t wc = a.zc;
   if (wc <= 0) {

@@ -106,6 +106,52 @@ def test_f32_pairs(hV, hT, conv, shape):
     assert np.array_equal(chi, chi_ref)
 
 
+@pytest.mark.parametrize("conv", ["V", "T"])
+@pytest.mark.parametrize("shape,kind", [
+    ((3, 4, 5, 130), "u8"), ((5, 9, 6, 129), "u8"), ((2, 5, 9, 257), "u16"),
+    ((4, 3, 3, 128), "f32"), ((3, 2, 7, 300), "f32"), ((6, 5, 11, 140), "f32")], ids=str)
+def test_4d_several_x_tiles(hV, hT, conv, shape, kind):
+    """4D rows wider than one 128-voxel tile, ragged in x, y and z: shared
+    histogram (u8), global histogram (u16, 65536 bins) and pairs (f32)."""
+    h = _handle(hV, hT, conv)
+    if kind == "u8":
+        img = synth.uniform_u8(shape, S + 55)
+        assert np.array_equal(ecc.ecc_compute(h, img), oracle.ecc_int(img, 256, conv))
+    elif kind == "u16":
+        img = synth.uniform_int(shape, 65536, S + 56, np.uint16)
+        assert np.array_equal(ecc.ecc_compute(h, img), oracle.ecc_int(img, 65536, conv))
+    else:
+        img = synth.grf_f32(shape, 1.5, S + 57)
+        t, chi = ecc.ecc_compute(h, img)
+        t_ref, chi_ref = oracle.ecc_pairs_float(img, conv)
+        assert np.array_equal(t, t_ref) and np.array_equal(chi, chi_ref)
+
+
+def test_f32_4d_full_size_properties(lib):
+    """The 128^4 float field of the benchmark: thresholds strictly
+    ascending, chi = 1 at the top (the full box is contractible), and the
+    value transform of the same image through the integer 4D path agrees with
+    the pairs at the top value of every 512th bin."""
+    d = synth.grf_f32_torch((128, 128, 128, 128), 3.0, synth.SEED_BASE + 4).contiguous()
+    lo, hi, bins = float(d.min()), float(d.max()), 4096
+    h = ecc.ecc_create(device=0)
+    try:
+        t, chi = ecc.ecc_compute(h, d)
+        q = ecc.ecc_compute_quantized(h, d, lo, hi, bins)
+    finally:
+        ecc.ecc_destroy(h)
+    assert np.all(np.diff(t) > 0) and chi[-1] == 1 and q[-1] == 1
+    import torch
+    vals = d.reshape(-1)
+    codes = torch.from_numpy(oracle.quantize_f32(vals.cpu().numpy(), lo, hi, bins)).cuda()
+    top = torch.full((bins,), float("-inf"), device="cuda")
+    top = top.scatter_reduce(0, codes, vals, reduce="amax")
+    top = torch.cummax(top, 0).values.cpu().numpy()
+    for k in range(0, bins, 512):
+        i = np.searchsorted(t, top[k], side="right") - 1
+        assert q[k] == (chi[i] if i >= 0 else 0)
+
+
 def test_f32_ties_and_signed_zero(hV):
     rng = np.random.default_rng(S + 51)
     img = (rng.integers(-3, 4, size=(10, 11, 12)) * 0.5).astype(np.float32)
@@ -246,3 +292,44 @@ def test_full_size_3d_512_smooth_device_path(hV):
     for lo in range(0, 513, 128):
         want += oracle.vcec_int_zrange(img, 256, lo, min(lo + 128, 513), "V")
     assert np.array_equal(got, oracle.ecc_from_vcec(want))
+
+
+@pytest.mark.parametrize("shape,dtype,bins", [
+    ((96, 400, 500), np.uint16, 16384),   # 38 MB: 9 chunks
+    ((2, 4096, 2048), np.uint8, 256),     # 16 MB in 2 planes: 2 chunks
+    ((20, 30, 100, 300), np.uint8, 256),  # 4D, generic kernel, chunked
+    ((70, 300, 800), np.uint8, 200),      # bins the bit-sliced kernel does not take
+], ids=str)
+def test_large_host_image_chunked_upload(shape, dtype, bins):
+    """Host images of 16 MB and more are uploaded in plane chunks overlapping
+    the kernels: the curve equals the one of the same bytes on the device
+    (uploaded whole), and the oracle's where it finishes quickly."""
+    import torch
+    rng = np.random.default_rng(S + 77)
+    img = rng.integers(0, bins, size=shape).astype(dtype)
+    h = ecc.ecc_create(device=0, bins=bins)
+    try:
+        got = ecc.ecc_compute(h, img)
+        raw = torch.from_numpy(img.view(np.int16) if dtype == np.uint16 else img).cuda()
+        d = raw.view(torch.uint16) if dtype == np.uint16 else raw
+        ref = ecc.ecc_compute(h, d)
+    finally:
+        ecc.ecc_destroy(h)
+    assert np.array_equal(got, ref)
+    assert got[-1] == 1
+    if shape == (2, 4096, 2048):
+        assert np.array_equal(got, oracle.ecc_int(img, bins, "V"))
+
+
+def test_large_host_image_value_error_in_a_late_chunk():
+    img = synth.smooth_u8((64, 512, 512), 2.0, S + 79).astype(np.uint16)
+    img[50, 7, 9] = 300
+    h = ecc.ecc_create(device=0, bins=256)
+    try:
+        with pytest.raises(ecc.EccError) as ei:
+            ecc.ecc_compute(h, img)
+        assert ei.value.status == ecc.ECC_ERR_VALUE
+        img[50, 7, 9] = 3
+        assert ecc.ecc_compute(h, img)[-1] == 1
+    finally:
+        ecc.ecc_destroy(h)

@@ -187,13 +187,14 @@ __device__ __forceinline__ uint32_t gcmp(uint32_t b, uint32_t cout, uint32_t nou
 
 }  // namespace bits
 
-// One tile (tile index t of geometry geo) of one image. All threads of the
-// block call it; blockDim.x = 32 * (geo.RB / geo.R). pl/g0/g1 are the
-// shared exchange arrays (record strides pl_rec (odd, >= NB + 1), 3, 7),
-// hist the shared histogram (kBitsSmem).
+// Planes [z0, z1) of the row column (tx, ty) of geometry geo, one image. All
+// threads of the block call it; blockDim.x = 32 * (geo.RB / geo.R). pl/g0/g1
+// are the shared exchange arrays (record strides pl_rec (odd, >= NB + 1), 3,
+// 7), hist the shared histogram (kBitsSmem).
 template <int NB, int CONV, int HM>
-__device__ void bits_tile(const BitsImg& im, const BitsGeo& geo, int64_t t, uint32_t* pl,
-                          uint32_t* g0, uint32_t* g1, int pl_rec, int* hist) {
+__device__ void bits_span(const BitsImg& im, const BitsGeo& geo, int64_t tx, int64_t ty,
+                          int64_t z0, int64_t z1, uint32_t* pl, uint32_t* g0, uint32_t* g1,
+                          int pl_rec, int* hist) {
   using namespace bits;
   constexpr int NP = NB;                // value planes
   constexpr int EB = NB <= 8 ? 1 : 2;   // bytes per voxel
@@ -209,12 +210,8 @@ __device__ void bits_tile(const BitsImg& im, const BitsGeo& geo, int64_t t, uint
   const size_t row_bytes = (size_t)im.row_pitch;
   const unsigned FULL = 0xFFFFFFFFu;
 
-  const int64_t txy = geo.tiles_x * geo.tiles_y;
-  const int64_t tz = t / txy, rem = t - tz * txy;
-  const int64_t ty = rem / geo.tiles_x, tx = rem - ty * geo.tiles_x;
   const int64_t y = ty * (RB - 2) - 1 + br;
   const int64_t x0 = (geo.modeB ? tx * 960 - 32 : 0) + 32 * (int64_t)l;
-  const int64_t z0 = im.w_lo + tz * geo.zc, z1 = min(z0 + geo.zc, im.w_hi);
   const bool row_in = y >= 0 && y < ny;
   uint32_t xin = 0;  // bits whose x lies inside the image
   if (x0 < nx && x0 + 32 > 0) {
@@ -559,6 +556,19 @@ __device__ void bits_tile(const BitsImg& im, const BitsGeo& geo, int64_t t, uint
     }
   }
   __syncthreads();
+}
+
+// Tile t of geometry geo: row column t mod (tiles_x * tiles_y), planes
+// [w_lo + tz * zc, + zc) with tz = t / (tiles_x * tiles_y).
+template <int NB, int CONV, int HM>
+__device__ __forceinline__ void bits_tile(const BitsImg& im, const BitsGeo& geo, int64_t t,
+                                          uint32_t* pl, uint32_t* g0, uint32_t* g1, int pl_rec,
+                                          int* hist) {
+  const int64_t txy = geo.tiles_x * geo.tiles_y;
+  const int64_t tz = t / txy, rem = t - tz * txy;
+  const int64_t ty = rem / geo.tiles_x, tx = rem - ty * geo.tiles_x;
+  const int64_t z0 = im.w_lo + tz * geo.zc, z1 = min(z0 + geo.zc, im.w_hi);
+  bits_span<NB, CONV, HM>(im, geo, tx, ty, z0, z1, pl, g0, g1, pl_rec, hist);
 }
 
 }  // namespace ecc

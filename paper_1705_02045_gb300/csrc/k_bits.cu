@@ -27,8 +27,25 @@ __device__ __forceinline__ void bits_blocks(const BitsImg& im, const BitsGeo& ge
   int* hist = reinterpret_cast<int*>(g1 + 2 * recs * kBitsG1Rec);
   if (HM == kBitsSmem)
     for (int64_t b = threadIdx.x; b < im.bins; b += blockDim.x) hist[b] = 0;
-  for (int64_t t = blockIdx.x; t < geo.n_tiles; t += gridDim.x)
-    bits_tile<NB, CONV, HM>(im, geo, t, pl, g0, g1, pl_rec, hist);
+  if (geo.zc > 0) {
+    for (int64_t t = blockIdx.x; t < geo.n_tiles; t += gridDim.x)
+      bits_tile<NB, CONV, HM>(im, geo, t, pl, g0, g1, pl_rec, hist);
+  } else {
+    // balanced: the row columns laid end to end along z, split into equal
+    // plane counts per block (a span may cross into the next column)
+    const int64_t wn = im.w_hi - im.w_lo, cols = geo.tiles_x * geo.tiles_y;
+    const int64_t total = cols * wn;
+    int64_t lo = total * blockIdx.x / gridDim.x;
+    const int64_t hi = total * (blockIdx.x + 1) / gridDim.x;
+    while (lo < hi) {
+      const int64_t col = lo / wn, z0 = lo - col * wn;
+      const int64_t z1 = min(wn, z0 + (hi - lo));
+      const int64_t ty = col / geo.tiles_x, tx = col - ty * geo.tiles_x;
+      bits_span<NB, CONV, HM>(im, geo, tx, ty, im.w_lo + z0, im.w_lo + z1, pl, g0, g1, pl_rec,
+                              hist);
+      lo += z1 - z0;
+    }
+  }
   if (HM == kBitsSmem) {
     __syncthreads();
     for (int64_t b = threadIdx.x; b < im.bins; b += blockDim.x) {
@@ -61,13 +78,16 @@ cudaError_t launch_t(const BitsImg& im, int W, int64_t zc, int grid_req, int num
   const int64_t grid_cap = (int64_t)per_sm * num_sms;
   const int64_t wn = im.w_hi - im.w_lo;
   BitsGeo g = bits_geo(im.n[2], im.n[1], wn, W, std::max<int64_t>(zc, 1));
+  int64_t grid;
   if (zc <= 0) {
-    // about two tiles per resident block, at least 16 planes per tile
-    const int64_t txy = g.tiles_x * g.tiles_y;
-    int64_t z = std::max<int64_t>(16, (wn * txy + 2 * grid_cap - 1) / (2 * grid_cap));
-    g = bits_geo(im.n[2], im.n[1], wn, W, std::min<int64_t>(z, std::max<int64_t>(wn, 1)));
+    // balanced spans: every resident block gets the same number of planes
+    // (at least 8, so the one priming plane per span stays small)
+    g.zc = 0;
+    const int64_t steps = g.tiles_x * g.tiles_y * wn;
+    grid = grid_req > 0 ? grid_req : std::max<int64_t>(1, std::min(grid_cap, steps / 8));
+  } else {
+    grid = grid_req > 0 ? grid_req : std::min(g.n_tiles, grid_cap);
   }
-  const int64_t grid = grid_req > 0 ? grid_req : std::min(g.n_tiles, grid_cap);
   kern<<<(unsigned)grid, threads, smem, stream>>>(im, g, pl_rec);
   ++*launches;
   return cudaGetLastError();

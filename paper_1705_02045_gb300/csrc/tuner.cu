@@ -3,7 +3,8 @@
 // For each shape class (value bits, lanes per row group, convention, and the
 // base-2 logarithms of the row count and of the plane count) the first image
 // of the class times a few launch shapes -- warps per block (rows per block)
-// and planes per tile, then block-private shared-memory histograms against
+// and planes per tile (or equal plane spans per block), then block-private
+// shared-memory histograms against
 // direct global atomics for the fastest shape -- on its own data, keeps the
 // fastest, and reuses it for every later image of the class. With
 // ecc_config.tuner_cache set, the table is read from and appended to that
@@ -56,7 +57,7 @@ void Tuner::load(const std::string& file) {
     const int got =
         std::sscanf(line, " {\"key\": \"%95[^\"]\", \"warps\": %d, \"zc\": %d, \"ms\": %f, \"hist\": %d",
                     k, &w, &z, &ms, &hm);
-    if (got >= 4 && w > 0 && z > 0) table[k] = TuneChoice{w, z, ms, got == 5 ? hm : 0};
+    if (got >= 4 && w > 0 && z >= 0) table[k] = TuneChoice{w, z, ms, got == 5 ? hm : 0};
   }
   std::fclose(f);
 }
@@ -107,7 +108,7 @@ int tune_bits(ecc_handle* h, const LocalArgs& base, TuneChoice* best) {
   };
   for (int W : {4, 8, 16}) {
     if (W * R < 3 || W * R > 512) continue;
-    for (int zc : {16, 32, 64, 128}) {
+    for (int zc : {0, 16, 32, 64, 128}) {  // 0: balanced spans
       if (zc > 2 * planes && zc != 16) continue;
       LocalArgs a = base;
       a.warps = W;

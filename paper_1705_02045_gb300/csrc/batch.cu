@@ -158,6 +158,8 @@ __device__ void bits_item(const BImage& im, const BItem& item, uint32_t* pl, uin
   bi.bins = im.bins;
   bi.vcec = im.vcec;
   bi.err = im.err;
+  bi.curve = nullptr;
+  bi.done = nullptr;
   for (int64_t t = item.tile_lo; t < item.tile_hi; ++t)
     bits_tile<NB, CONV, HM>(bi, im.geo, t, pl, g0, g1, kBatchPlRec, hist);
 }

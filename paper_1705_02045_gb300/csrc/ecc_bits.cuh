@@ -56,6 +56,8 @@ struct BitsImg {
   int64_t bins;
   long long* vcec;
   int* err;
+  long long* curve;    // non-null: the last block writes the curve, zeroes vcec and *done
+  unsigned int* done;  // blocks finished (starts at 0)
 };
 
 enum BitsHist : int { kBitsSmem = 0, kBitsGlobal = 1 };

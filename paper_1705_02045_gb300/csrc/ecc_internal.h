@@ -47,6 +47,10 @@ struct LocalArgs {
   int warps = 0;                // bit-sliced kernel: warps per block (0 = auto)
   int hist = 0;                 // bit-sliced kernel histogram: 0 auto (shared memory when
                                 // bins <= kSmemBinsMax), 1 shared memory, 2 global atomics
+  long long* fused_curve = nullptr;  // bit-sliced kernel: the last block to finish writes
+                                     // the curve (prefix sum of vcec), then zeroes vcec and
+                                     // *done (which must start at 0)
+  unsigned int* done = nullptr;
   cudaStream_t stream = nullptr;
 };
 

@@ -134,13 +134,20 @@ int stage_image(ecc_handle* h, const void* image, bool on_device, const Shape& s
 // Host images of at least this many bytes are uploaded in plane chunks that
 // overlap with the computation (ecc_compute); at most kUploadChunksMax chunks.
 constexpr size_t kChunkedUploadBytes = size_t(16) << 20;
+constexpr int64_t kFusedScanBins = 2048;
 constexpr int64_t kUploadChunksMax = 16;
 
 int enqueue_int(ecc_handle* h, const void* d_img, int64_t row_pitch, const Shape& s, int dtype,
                 int64_t bins, long long* d_vcec, long long* d_curve, cudaStream_t stream,
                 const int64_t* chunk_end, const cudaEvent_t* chunk_ev, int n_chunks) {
-  cudaError_t e = cudaMemsetAsync(d_vcec, 0, sizeof(long long) * bins, stream);
-  if (e != cudaSuccess) return cuda_err(h, e, "memset vcec");
+  cudaError_t e;
+  if (!(d_vcec == h->clean_vcec && bins <= h->clean_bins)) {
+    if ((e = cudaMemsetAsync(d_vcec, 0, sizeof(long long) * bins, stream)))
+      return cuda_err(h, e, "memset vcec");
+    if (h->clean_vcec != d_vcec) h->clean_bins = 0;
+    h->clean_vcec = d_vcec;
+    h->clean_bins = std::max(h->clean_bins, bins);
+  }
   if (s.voxels > 0) {
     LocalArgs a;
     a.img = d_img;
@@ -181,6 +188,20 @@ int enqueue_int(ecc_handle* h, const void* d_img, int64_t row_pitch, const Shape
       a.zc = c.zc;
       a.hist = c.hist;
     }
+    // one bit-sliced launch over the whole image: its last block also writes
+    // the curve and leaves VCEC and the block counter at zero, so neither the
+    // clearing memset nor the scan launch is needed while that holds (up to
+    // kFusedScanBins bins: one block scans them after all others finished,
+    // which for larger histograms costs more than a separate 1024-thread scan)
+    const bool fused = n_chunks == 0 && a.n[0] <= step && h->variant != 1 && a.view == 3 &&
+                       bins <= kFusedScanBins &&
+                       bits_nb(dtype, bins) != 0 && row_pitch == 0 &&
+                       (dtype == kU8 || (reinterpret_cast<uintptr_t>(d_img) & 1u) == 0) &&
+                       h->done.p != nullptr;
+    if (fused) {
+      a.fused_curve = d_curve;
+      a.done = h->done.as<unsigned int>();
+    }
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (h->prof_on) {
       if ((e = cudaEventCreate(&ev0)) || (e = cudaEventCreate(&ev1)) ||
@@ -206,7 +227,13 @@ int enqueue_int(ecc_handle* h, const void* d_img, int64_t row_pitch, const Shape
       if ((e = cudaEventRecord(ev1, stream))) return cuda_err(h, e, "profiling event");
       h->prof_events.emplace_back(ev0, ev1);
     }
+    if (fused) {
+      h->clean_vcec = d_vcec;
+      h->clean_bins = std::max(h->clean_bins, bins);
+      return ECC_OK;
+    }
   }
+  h->clean_vcec = nullptr;
   int64_t cnt = 0;
   e = launch_scan(d_vcec, d_curve, bins, stream, &cnt);
   h->launches += cnt;
@@ -398,6 +425,8 @@ int ecc_create(const ecc_config* cfg, ecc_handle** out) {
       (e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking)) ||
       (e = h->errw.ensure(sizeof(int))) ||
       (e = cudaMemset(h->errw.p, 0, sizeof(int))) ||
+      (e = h->done.ensure(sizeof(unsigned int))) ||
+      (e = cudaMemset(h->done.p, 0, sizeof(unsigned int))) ||
       (e = cudaMallocHost(&h->h_err, sizeof(int)))) {
     g_create_err = std::string("CUDA setup: ") + cudaGetErrorString(e);
     ecc_destroy(h);
@@ -418,7 +447,7 @@ void ecc_destroy(ecc_handle* h) {
   if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
   for (DevBuf* b : {&h->img, &h->vcec, &h->curve, &h->errw, &h->pairs, &h->pair_count, &h->tmp,
                     &h->out_keys, &h->out_chi, &h->out_count, &h->batch_desc, &h->batch_items,
-                    &h->batch_vcec, &h->batch_curve, &h->codes})
+                    &h->batch_vcec, &h->batch_curve, &h->codes, &h->done})
     b->release();
   for (auto& pr : h->prof_events) {
     cudaEventDestroy(pr.first);

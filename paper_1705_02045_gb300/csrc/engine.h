@@ -90,6 +90,9 @@ struct ecc_handle {
 
   ecc::DevBuf img, vcec, curve, errw, pairs, pair_count, tmp, out_keys, out_chi, out_count;
   ecc::DevBuf codes;                    // value-transform codes (ecc_compute_quantized)
+  ecc::DevBuf done;                     // block counter of the fused curve scan (kept at 0)
+  const void* clean_vcec = nullptr;     // vcec buffer known to be zero on its first
+  int64_t clean_bins = 0;               // clean_bins entries (fused launches keep it so)
   ecc::DevBuf batch_desc, batch_items, batch_vcec, batch_curve;
   int* h_err = nullptr;                 // pinned scalar for error readback
   std::vector<cudaEvent_t> up_ev;       // chunked host-image upload (ecc_compute)

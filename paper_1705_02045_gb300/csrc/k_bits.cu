@@ -17,6 +17,43 @@ constexpr int kBitsWarps = 16;
 
 // Persistent blocks over the tiles of one image, each with a private
 // histogram added to the VCEC at the end.
+// Post-processing fused into the contribution launch (Sec. 3 "Post-Processing":
+// the curve is the running sum of the VCEC): the block that finishes last
+// scans the VCEC into the curve and leaves VCEC and counter at zero for the
+// next launch. Any block size that is a multiple of 32.
+__device__ void scan_and_clear(long long* vcec, long long* curve, int64_t bins) {
+  __shared__ long long wt[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  long long carry = 0;
+  for (int64_t base = 0; base < bins; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    long long v = i < bins ? __ldcg(vcec + i) : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long n = __shfl_up_sync(0xFFFFFFFFu, v, o);
+      if (lane >= o) v += n;
+    }
+    if (lane == 31) wt[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+      long long w = lane < nw ? wt[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const long long n = __shfl_up_sync(0xFFFFFFFFu, w, o);
+        if (lane >= o) w += n;
+      }
+      wt[lane] = w;
+    }
+    __syncthreads();
+    if (i < bins) {
+      curve[i] = carry + v + (warp > 0 ? wt[warp - 1] : 0);
+      vcec[i] = 0;
+    }
+    carry += wt[nw - 1];
+    __syncthreads();
+  }
+}
+
 template <int NB, int CONV, int HM>
 __device__ __forceinline__ void bits_blocks(const BitsImg& im, const BitsGeo& geo, int pl_rec) {
   extern __shared__ __align__(16) uint32_t sm[];
@@ -54,6 +91,18 @@ __device__ __forceinline__ void bits_blocks(const BitsImg& im, const BitsGeo& ge
                        (unsigned long long)(long long)v);
     }
   }
+  if (im.curve) {
+    __shared__ int last;
+    __threadfence();  // this thread's VCEC atomics before the block's ticket
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(im.done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      scan_and_clear(im.vcec, im.curve, im.bins);
+      if (threadIdx.x == 0) *im.done = 0u;
+    }
+  }
 }
 
 template <int NB, int CONV, int HM>
@@ -81,10 +130,12 @@ cudaError_t launch_t(const BitsImg& im, int W, int64_t zc, int grid_req, int num
   int64_t grid;
   if (zc <= 0) {
     // balanced spans: every resident block gets the same number of planes
-    // (at least 8, so the one priming plane per span stays small)
+    // (at least 8 where the image has enough, so the one priming plane per
+    // span stays small; at least one block per row column for thin images)
     g.zc = 0;
-    const int64_t steps = g.tiles_x * g.tiles_y * wn;
-    grid = grid_req > 0 ? grid_req : std::max<int64_t>(1, std::min(grid_cap, steps / 8));
+    const int64_t cols = g.tiles_x * g.tiles_y, steps = cols * wn;
+    grid = grid_req > 0 ? grid_req
+                        : std::max<int64_t>(1, std::min(grid_cap, std::max(cols, steps / 8)));
   } else {
     grid = grid_req > 0 ? grid_req : std::min(g.n_tiles, grid_cap);
   }
@@ -139,6 +190,8 @@ cudaError_t launch_local_bits(const LocalArgs& a, int num_sms, int64_t* launches
   im.bins = a.bins;
   im.vcec = a.vcec;
   im.err = a.err;
+  im.curve = a.fused_curve;
+  im.done = a.done;
   // 16 rows per block by default (8 warps of two 16-lane row groups for rows
   // of <= 512 voxels, 16 warps for rows wider than 1024); a.warps overrides
   int L = 1;

@@ -169,8 +169,9 @@ def test_bits_full_size_512_cube():
 def test_tuner_picks_and_caches_a_launch_shape(tmp_path):
     """The first image of a shape class tunes the bit-sliced launch shape
     (extra timed launches) and writes the choice to the cache file; a new
-    handle on the same file reuses it (exactly two launches: contribution and
-    scan). Results are the oracle's either way."""
+    handle on the same file reuses it (exactly one launch: the contribution
+    kernel, whose last block also writes the curve). Results are the oracle's
+    either way."""
     path = str(tmp_path / "tune.jsonl").encode()
     img = synth.smooth_u8((40, 60, 64), 2.0, S + 19)
     want = oracle.ecc_int(img, 256, "V")
@@ -187,7 +188,7 @@ def test_tuner_picks_and_caches_a_launch_shape(tmp_path):
     h = ecc.ecc_create(device=0, tuner_cache=path)
     try:
         assert np.array_equal(ecc.ecc_compute(h, img), want)
-        assert ecc.ecc_launch_count(h) == 2
+        assert ecc.ecc_launch_count(h) == 1
     finally:
         ecc.ecc_destroy(h)
 
@@ -247,3 +248,44 @@ def test_full_size_14bit_volume_streamed_resident_generic():
     finally:
         ecc.ecc_destroy(hb)
     assert np.array_equal(got, oracle.ecc_int(part, 16384, "V"))
+
+
+def test_fused_scan_interleaved_with_other_paths():
+    """The bit-sliced launch writes the curve from its last block and leaves the
+    VCEC at zero for the next call, which then skips the clearing memset; calls
+    of other paths (4D generic, other bin counts, value errors) in between
+    must not leak into it. Device calls back to back on one stream."""
+    import torch
+    a = synth.smooth_u8((20, 30, 64), 2.0, S + 70)
+    b = synth.uniform_u8((4, 5, 6, 7), S + 71)
+    c = synth.two_phase_u16((9, 21, 40), 1.5, S + 72)
+    bad = a.copy().astype(np.uint16)
+    bad[3, 4, 5] = 300
+    h = ecc.ecc_create(device=0)
+    h16 = ecc.ecc_create(device=0, bins=16384)
+    try:
+        for _ in range(2):
+            assert np.array_equal(ecc.ecc_compute(h, a), oracle.ecc_int(a, 256, "V"))
+            assert np.array_equal(ecc.ecc_compute(h, b), oracle.ecc_int(b, 256, "V"))
+            assert np.array_equal(ecc.ecc_compute(h16, c), oracle.ecc_int(c, 16384, "V"))
+            assert np.array_equal(ecc.ecc_compute(h, c), oracle.ecc_int(c, 65536, "V"))
+            assert np.array_equal(ecc.ecc_compute(h, a), oracle.ecc_int(a, 256, "V"))
+        hb = ecc.ecc_create(device=0, bins=256)
+        try:
+            with pytest.raises(ecc.EccError):
+                ecc.ecc_compute(hb, bad)
+            assert np.array_equal(ecc.ecc_compute(hb, a), oracle.ecc_int(a, 256, "V"))
+        finally:
+            ecc.ecc_destroy(hb)
+        st = torch.cuda.Stream()
+        d = torch.from_numpy(a).cuda()
+        curves = [torch.empty(256, dtype=torch.int64, device="cuda") for _ in range(4)]
+        for cv in curves:
+            ecc.ecc_compute_device(h, d, 256, cv, stream=st)
+        st.synchronize()
+        want = oracle.ecc_int(a, 256, "V")
+        for cv in curves:
+            assert np.array_equal(cv.cpu().numpy(), want)
+    finally:
+        ecc.ecc_destroy(h)
+        ecc.ecc_destroy(h16)

@@ -12,6 +12,7 @@
 #include "ecc_tile.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace ecc {
 
@@ -66,6 +67,29 @@ k_local3(const LocalArgs a, int64_t zc, int64_t tiles_x, int64_t tiles_y, int64_
 constexpr int k4TX = 128, k4TY = 4, k4TZ = 2, k4VX = 4;
 constexpr int k4PW = 132, k4PH = k4TY + 2, k4PD = k4TZ + 2, k4PL = k4PW * k4PH * k4PD;
 static_assert(k4TX / k4VX * k4TY * k4TZ == kThreads, "one thread per 4 voxels");
+
+// Float images keep their values (as bits) in the halo ring, +inf outside, and
+// compare them as floats: the same order as the keys (-0 equals +0, NaN is
+// rejected); the compare is a set.* (0 or -1) and the bit goes in by an
+// integer multiply-add on the FMA pipe (measured 6.4 -> 5.9 ms on 128^4).
+// Integer images keep their keys and the compare-select-or form (the
+// multiply-add form measured slower there).
+template <typename T>
+constexpr bool kFloatRing = std::is_same<T, float>::value;
+
+template <typename T, bool kForward>
+__device__ __forceinline__ uint32_t add_after(uint32_t m, uint32_t ku, uint32_t kv, int bit) {
+  if constexpr (kFloatRing<T>) {
+    uint32_t s;
+    if (kForward)
+      asm("set.ge.u32.f32 %0, %1, %2;" : "=r"(s) : "f"(__uint_as_float(ku)), "f"(__uint_as_float(kv)));
+    else
+      asm("set.gt.u32.f32 %0, %1, %2;" : "=r"(s) : "f"(__uint_as_float(ku)), "f"(__uint_as_float(kv)));
+    return m - s * (1u << bit);
+  } else {
+    return m | (after<kForward>(ku, kv) << bit);
+  }
+}
 
 __device__ __forceinline__ void load6(const uint32_t* p, uint32_t k[6]) {
   const uint4 q = *reinterpret_cast<const uint4*>(p);
@@ -159,11 +183,14 @@ k_local4(const LocalArgs a, int64_t wc, int64_t tiles_x, int64_t tiles_y, int64_
         for (int k = 0; k < kKeysPerLane; ++k) {
           const int lx = lane + 32 * k;
           if (lx >= kRowKeys) continue;
-          uint32_t key = kOutside;
+          uint32_t key = kFloatRing<T> ? 0x7F800000u : kOutside;  // +inf / above every key
           if ((f.in >> (i * kKeysPerLane + k)) & 1u) {
             const T v = f.v[i][k];
             if (value_bad(v)) atomicOr(a.err, kErrValue);
-            key = value_key(v);
+            if constexpr (kFloatRing<T>)
+              key = __float_as_uint(v);
+            else
+              key = value_key(v);
           }
           dst[row * k4PW + lx] = key;
         }
@@ -213,10 +240,10 @@ k_local4(const LocalArgs a, int64_t wc, int64_t tiles_x, int64_t tiles_y, int64_
             for (int j = 0; j < k4VX; ++j) {
               const uint32_t kv = kc[j + 1];
               if (centre) continue;
-              M0[j] |= (fwd ? after<true>(r0[j + 1 + dx], kv) : after<false>(r0[j + 1 + dx], kv))
-                       << bit;
-              Mp[j] |= after<true>(rp[j + 1 + dx], kv) << bit;
-              Mm[j] |= after<false>(rm[j + 1 + dx], kv) << bit;
+              M0[j] = fwd ? add_after<T, true>(M0[j], r0[j + 1 + dx], kv, bit)
+                          : add_after<T, false>(M0[j], r0[j + 1 + dx], kv, bit);
+              Mp[j] = add_after<T, true>(Mp[j], rp[j + 1 + dx], kv, bit);
+              Mm[j] = add_after<T, false>(Mm[j], rm[j + 1 + dx], kv, bit);
             }
           }
         }
@@ -228,7 +255,8 @@ k_local4(const LocalArgs a, int64_t wc, int64_t tiles_x, int64_t tiles_y, int64_
       for (int j = 0; j < k4VX; ++j) {
         const uint32_t kv = kc[j + 1];
         uint32_t m0 = M0[j], mp = Mp[j], mm = Mm[j];
-        uint32_t bp = after<true>(kp[j + 1], kv), bm = after<false>(km[j + 1], kv);
+        uint32_t bp = add_after<T, true>(0u, kp[j + 1], kv, 0);
+        uint32_t bm = add_after<T, false>(0u, km[j + 1], kv, 0);
         if (CONV == kConvT) {
           m0 = ~m0 & 0x3FFFFFFu;
           mp = ~mp & 0x3FFFFFFu;
@@ -240,7 +268,8 @@ k_local4(const LocalArgs a, int64_t wc, int64_t tiles_x, int64_t tiles_y, int64_
         if (bp) g -= g3_of_mask(m0 & mp, g2);
         if (bm) g -= g3_of_mask(m0 & mm, g2);
         // (-1)^4 G_4 for V; G_4 of the complement for T
-        deposit<MODE>(row_valid && gx0 + j < nx, kv, g, s);
+        const uint32_t key = kFloatRing<T> ? value_key(__uint_as_float(kv)) : kv;
+        deposit<MODE>(row_valid && gx0 + j < nx, key, g, s);
       }
       // slot (w + 2) & 3 held volume w - 2, which nobody reads after the
       // previous step's barrier

@@ -247,6 +247,7 @@ struct Slot {
   cudaGraphExec_t exec_small = nullptr, exec_large = nullptr;
   cudaEvent_t done = nullptr;
   cudaEvent_t t0 = nullptr, t1 = nullptr;  // around the graph, for the online tuner
+  std::vector<size_t> res_off;             // byte offset of each image's curve in h_arena
   int tune_cand = -1;                      // candidate timed by the last run, or -1
   double tune_vox = 0;                     // its bit-sliced voxels
 };
@@ -451,20 +452,27 @@ int slot_run(ecc_handle* h, Slot& sl, BatchTune& tune, const std::vector<ImgSpec
   const int depth = tune_depth(tune, sl);
   double bits_vox = 0;
   bool large = false;
-  size_t arena_total = 0;
-  for (const ImgSpec& sp : specs) {
+  // device arena: all VCECs, then all (curve, error word) records, so that
+  // only the second part is copied back
+  size_t vcec_total = 0, res_total = 0;
+  sl.res_off.resize(n);
+  for (int i = 0; i < n; ++i) {
+    const ImgSpec& sp = specs[i];
     if (sp.bins > kSmallBins && sp.bins <= kSmemBinsMax) large = true;
-    arena_total += arena_bytes(sp.bins);
+    vcec_total += sizeof(long long) * sp.bins;
+    sl.res_off[i] = res_total;
+    res_total += sizeof(long long) * (sp.bins + 1);
   }
+  const size_t arena_total = vcec_total + res_total;
   if ((e = sl.arena.ensure(arena_total))) return cuda_err(h, e, "batch arena");
-  if (sl.h_arena_cap < arena_total) {
+  if (sl.h_arena_cap < res_total) {
     if (sl.h_arena) cudaFreeHost(sl.h_arena);
     sl.h_arena = nullptr;
-    if ((e = cudaMallocHost(&sl.h_arena, arena_total))) {
+    if ((e = cudaMallocHost(&sl.h_arena, res_total))) {
       sl.h_arena_cap = 0;
       return cuda_err(h, e, "pinned arena");
     }
-    sl.h_arena_cap = arena_total;
+    sl.h_arena_cap = res_total;
   }
   BHeader* hdr = reinterpret_cast<BHeader*>(sl.h_desc + sl.L.hdr);
   BImage* imgs = reinterpret_cast<BImage*>(sl.h_desc + sl.L.imgs);
@@ -483,9 +491,9 @@ int slot_run(ecc_handle* h, Slot& sl, BatchTune& tune, const std::vector<ImgSpec
     im.bins = sp.bins;
     im.dtype = sp.dtype;
     im.vcec = reinterpret_cast<long long*>(abase + off);
-    im.curve = im.vcec + sp.bins;
+    im.curve = reinterpret_cast<long long*>(abase + vcec_total + sl.res_off[i]);
     im.err = reinterpret_cast<int*>(im.curve + sp.bins);
-    off += arena_bytes(sp.bins);
+    off += sizeof(long long) * sp.bins;
     const int64_t vox = sp.n[0] * sp.n[1] * sp.n[2];
     if (vox == 0) continue;
     im.nb = image_nb(h, sp);
@@ -498,7 +506,10 @@ int slot_run(ecc_handle* h, Slot& sl, BatchTune& tune, const std::vector<ImgSpec
       const int64_t width = im.geo.modeB ? 1024 : 32 * im.geo.L;
       ib.push_back(i);
       tb.push_back(im.geo.n_tiles);
-      cb.push_back((im.geo.zc + 1) * im.geo.RB * width);
+      // logic work grows with the value planes: ~9 ops per voxel at 8 bits,
+      // ~14 at 14, ~16 at 16 (plus one priming plane per tile)
+      const int64_t weight = im.nb == 8 ? 9 : im.nb == 14 ? 14 : 16;
+      cb.push_back((im.geo.zc + 1) * im.geo.RB * width * weight);
     } else {
       im.tiles_x = (sp.n[2] + kT3X - 1) / kT3X;
       im.tiles_y = (sp.n[1] + kT3Y - 1) / kT3Y;
@@ -506,7 +517,7 @@ int slot_run(ecc_handle* h, Slot& sl, BatchTune& tune, const std::vector<ImgSpec
       const int64_t tz = (sp.n[0] + im.zc - 1) / im.zc;
       ig.push_back(i);
       tg.push_back(im.tiles_x * im.tiles_y * tz);
-      cg.push_back((int64_t)kT3X * kT3Y * (im.zc + 2) * 12);  // generic: ~12x per voxel
+      cg.push_back((int64_t)kT3X * kT3Y * (im.zc + 2) * 12 * 9);  // generic: ~12x per voxel
     }
   }
   BItem* items_b = reinterpret_cast<BItem*>(sl.h_desc + sl.L.items_b);
@@ -536,7 +547,7 @@ int slot_run(ecc_handle* h, Slot& sl, BatchTune& tune, const std::vector<ImgSpec
     if (bits_vox > 0) sl.tune_vox = bits_vox;
     else sl.tune_cand = -1;  // nothing to learn from a batch without bit-sliced images
   }
-  if ((e = cudaMemcpyAsync(sl.h_arena, sl.arena.p, arena_total, cudaMemcpyDeviceToHost,
+  if ((e = cudaMemcpyAsync(sl.h_arena, abase + vcec_total, res_total, cudaMemcpyDeviceToHost,
                            sl.stream)) ||
       (e = cudaEventRecord(sl.done, sl.stream)))
     return cuda_err(h, e, "copy results");
@@ -545,16 +556,14 @@ int slot_run(ecc_handle* h, Slot& sl, BatchTune& tune, const std::vector<ImgSpec
 
 // Image i's curve out of the slot's pinned arena; status from its error word.
 int slot_result(const Slot& sl, const std::vector<ImgSpec>& specs, int i, int64_t** curve) {
-  size_t off = 0;
-  for (int j = 0; j < i; ++j) off += arena_bytes(specs[j].bins);
-  const long long* rec = reinterpret_cast<const long long*>(sl.h_arena + off);
+  const long long* rec = reinterpret_cast<const long long*>(sl.h_arena + sl.res_off[i]);
   const int64_t bins = specs[i].bins;
-  const int err = *reinterpret_cast<const int*>(rec + 2 * bins);
+  const int err = *reinterpret_cast<const int*>(rec + bins);
   if (err & kErrValue) return ECC_ERR_VALUE;
   if (err & kErrOverflow) return ECC_ERR_CUDA;
   *curve = static_cast<int64_t*>(std::malloc(sizeof(int64_t) * std::max<int64_t>(bins, 1)));
   if (!*curve) return ECC_ERR_OOM;
-  std::memcpy(*curve, rec + bins, sizeof(int64_t) * bins);
+  std::memcpy(*curve, rec, sizeof(int64_t) * bins);
   return ECC_OK;
 }
 

@@ -492,10 +492,12 @@ __device__ void bits_span(const BitsImg& im, const BitsGeo& geo, int64_t tx, int
       // change = N - 13; zero iff N == 0b01101
       const uint32_t eq13 = ~n4 & n3 & n2 & ~n1 & n0;
       uint32_t nzm = ~eq13 & dep;
+      // bins = 2^NB here; a value with bits above NB has already set the
+      // value error (make_planes), so masking only keeps its (discarded)
+      // deposit inside the histogram
       auto deposit = [&](uint32_t v, int c) {
-        if ((int64_t)v >= im.bins) {
-          atomicOr(im.err, kErrValue);
-        } else if (HM == kBitsSmem) {
+        v &= (1u << NB) - 1u;
+        if (HM == kBitsSmem) {
           atomicAdd(&hist[v], c);
         } else {
           atomicAdd(reinterpret_cast<unsigned long long*>(im.vcec) + v,

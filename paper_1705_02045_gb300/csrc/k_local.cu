@@ -68,40 +68,6 @@ constexpr int k4TX = 128, k4TY = 4, k4TZ = 2, k4VX = 4;
 constexpr int k4PW = 132, k4PH = k4TY + 2, k4PD = k4TZ + 2, k4PL = k4PW * k4PH * k4PD;
 static_assert(k4TX / k4VX * k4TY * k4TZ == kThreads, "one thread per 4 voxels");
 
-// Float images keep their values (as bits) in the halo ring, +inf outside, and
-// compare them as floats: the same order as the keys (-0 equals +0, NaN is
-// rejected); the compare is a set.* (0 or -1) and the bit goes in by an
-// integer multiply-add on the FMA pipe (measured 6.4 -> 5.9 ms on 128^4).
-// Integer images keep their keys and the compare-select-or form (the
-// multiply-add form measured slower there).
-template <typename T>
-constexpr bool kFloatRing = std::is_same<T, float>::value;
-
-template <typename T, bool kForward>
-__device__ __forceinline__ uint32_t add_after(uint32_t m, uint32_t ku, uint32_t kv, int bit) {
-  if constexpr (kFloatRing<T>) {
-    uint32_t s;
-    if (kForward)
-      asm("set.ge.u32.f32 %0, %1, %2;" : "=r"(s) : "f"(__uint_as_float(ku)), "f"(__uint_as_float(kv)));
-    else
-      asm("set.gt.u32.f32 %0, %1, %2;" : "=r"(s) : "f"(__uint_as_float(ku)), "f"(__uint_as_float(kv)));
-    return m - s * (1u << bit);
-  } else {
-    return m | (after<kForward>(ku, kv) << bit);
-  }
-}
-
-__device__ __forceinline__ void load6(const uint32_t* p, uint32_t k[6]) {
-  const uint4 q = *reinterpret_cast<const uint4*>(p);
-  const uint2 r = *reinterpret_cast<const uint2*>(p + 4);
-  k[0] = q.x;
-  k[1] = q.y;
-  k[2] = q.z;
-  k[3] = q.w;
-  k[4] = r.x;
-  k[5] = r.y;
-}
-
 template <typename T, int CONV, int MODE>
 __global__ void __launch_bounds__(kThreads, 2)
 k_local4(const LocalArgs a, int64_t wc, int64_t tiles_x, int64_t tiles_y, int64_t tiles_z,
@@ -183,11 +149,11 @@ k_local4(const LocalArgs a, int64_t wc, int64_t tiles_x, int64_t tiles_y, int64_
         for (int k = 0; k < kKeysPerLane; ++k) {
           const int lx = lane + 32 * k;
           if (lx >= kRowKeys) continue;
-          uint32_t key = kFloatRing<T> ? 0x7F800000u : kOutside;  // +inf / above every key
+          uint32_t key = kFloatRing3<T> ? 0x7F800000u : kOutside;  // +inf / above every key
           if ((f.in >> (i * kKeysPerLane + k)) & 1u) {
             const T v = f.v[i][k];
             if (value_bad(v)) atomicOr(a.err, kErrValue);
-            if constexpr (kFloatRing<T>)
+            if constexpr (kFloatRing3<T>)
               key = __float_as_uint(v);
             else
               key = value_key(v);
@@ -216,7 +182,7 @@ k_local4(const LocalArgs a, int64_t wc, int64_t tiles_x, int64_t tiles_y, int64_
       const uint32_t* v0 = ring + (int)(w & 3) * k4PL;
       const uint32_t* vp = ring + (int)((w + 1) & 3) * k4PL;
       uint32_t kc[6];
-      load6(v0 + c0, kc);
+      load6_3(v0 + c0, kc);
       // 26-bit masks (layout of g3_of_mask) of the volumes w, w+1, w-1 for
       // the 4 voxels j (key kc[j + 1]), and the straight neighbours along w
       uint32_t M0[k4VX] = {}, Mp[k4VX] = {}, Mm[k4VX] = {};
@@ -226,9 +192,9 @@ k_local4(const LocalArgs a, int64_t wc, int64_t tiles_x, int64_t tiles_y, int64_
         for (int dy = -1; dy <= 1; ++dy) {
           const int o = c0 + (dz * k4PH + dy) * k4PW;
           uint32_t r0[6], rp[6], rm[6];
-          load6(v0 + o, r0);
-          load6(vp + o, rp);
-          load6(vm + o, rm);
+          load6_3(v0 + o, r0);
+          load6_3(vp + o, rp);
+          load6_3(vm + o, rm);
 #pragma unroll
           for (int dx = -1; dx <= 1; ++dx) {
             const bool centre = dz == 0 && dy == 0 && dx == 0;
@@ -240,23 +206,23 @@ k_local4(const LocalArgs a, int64_t wc, int64_t tiles_x, int64_t tiles_y, int64_
             for (int j = 0; j < k4VX; ++j) {
               const uint32_t kv = kc[j + 1];
               if (centre) continue;
-              M0[j] = fwd ? add_after<T, true>(M0[j], r0[j + 1 + dx], kv, bit)
-                          : add_after<T, false>(M0[j], r0[j + 1 + dx], kv, bit);
-              Mp[j] = add_after<T, true>(Mp[j], rp[j + 1 + dx], kv, bit);
-              Mm[j] = add_after<T, false>(Mm[j], rm[j + 1 + dx], kv, bit);
+              M0[j] = fwd ? add_after3<T, true>(M0[j], r0[j + 1 + dx], kv, bit)
+                          : add_after3<T, false>(M0[j], r0[j + 1 + dx], kv, bit);
+              Mp[j] = add_after3<T, true>(Mp[j], rp[j + 1 + dx], kv, bit);
+              Mm[j] = add_after3<T, false>(Mm[j], rm[j + 1 + dx], kv, bit);
             }
           }
         }
       // straight neighbours along w (same x, y, z)
       uint32_t kp[6], km[6];
-      load6(vp + c0, kp);
-      load6(vm + c0, km);
+      load6_3(vp + c0, kp);
+      load6_3(vm + c0, km);
 #pragma unroll
       for (int j = 0; j < k4VX; ++j) {
         const uint32_t kv = kc[j + 1];
         uint32_t m0 = M0[j], mp = Mp[j], mm = Mm[j];
-        uint32_t bp = add_after<T, true>(0u, kp[j + 1], kv, 0);
-        uint32_t bm = add_after<T, false>(0u, km[j + 1], kv, 0);
+        uint32_t bp = add_after3<T, true>(0u, kp[j + 1], kv, 0);
+        uint32_t bm = add_after3<T, false>(0u, km[j + 1], kv, 0);
         if (CONV == kConvT) {
           m0 = ~m0 & 0x3FFFFFFu;
           mp = ~mp & 0x3FFFFFFu;
@@ -268,7 +234,7 @@ k_local4(const LocalArgs a, int64_t wc, int64_t tiles_x, int64_t tiles_y, int64_
         if (bp) g -= g3_of_mask(m0 & mp, g2);
         if (bm) g -= g3_of_mask(m0 & mm, g2);
         // (-1)^4 G_4 for V; G_4 of the complement for T
-        const uint32_t key = kFloatRing<T> ? value_key(__uint_as_float(kv)) : kv;
+        const uint32_t key = kFloatRing3<T> ? value_key(__uint_as_float(kv)) : kv;
         deposit<MODE>(row_valid && gx0 + j < nx, key, g, s);
       }
       // slot (w + 2) & 3 held volume w - 2, which nobody reads after the
@@ -294,7 +260,7 @@ cudaError_t launch_typed(const LocalArgs& a, int num_sms, int64_t* launches) {
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
     if (e != cudaSuccess) return e;
-    const int64_t tiles_x = (a.n[2] + 31) / 32, tiles_y = (a.n[1] + 7) / 8;
+    const int64_t tiles_x = (a.n[2] + kT3X - 1) / kT3X, tiles_y = (a.n[1] + kT3Y - 1) / kT3Y;
     const int64_t grid_cap = (int64_t)std::max(per_sm, 1) * num_sms;
     int64_t zc = a.zc;
     if (zc <= 0) {

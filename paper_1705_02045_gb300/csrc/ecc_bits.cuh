@@ -204,7 +204,11 @@ __device__ void bits_span(const BitsImg& im, const BitsGeo& geo, int64_t tx, int
   const int L = geo.L, RB = geo.RB;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int grp = lane / L, l = lane - grp * L;
-  const int br = warp * geo.R + grp;    // row within the block, 0..RB-1
+  // row within the block, 0..RB-1: the two collar rows (0 and RB-1) share the
+  // first warp (row groups 0 and 1), so the other warps hold own rows only
+  // and the collar warp skips what collar rows do not need
+  const int slot = warp * geo.R + grp;
+  const int br = slot == 0 ? 0 : slot == 1 ? RB - 1 : slot - 1;
   const int my = br * L + l;
   const int up = (br + 1 < RB ? br + 1 : br) * L + l;  // clamped neighbour rows
   const int dn = (br > 0 ? br - 1 : br) * L + l;
@@ -415,6 +419,7 @@ __device__ void bits_span(const BitsImg& im, const BitsGeo& geo, int64_t tx, int
 #pragma unroll
     for (int i = 0; i < 3; ++i) Gp[i] = G1[1][i];
 
+    // (warp-uniform in the collar warp, whose lanes all have dep = 0)
     if (z >= z0 && dep) {
       // b(dz, dy, dx): after-bits (V) or their complement (T)
       auto b = [&](int dz, int dy, int dx) -> uint32_t {

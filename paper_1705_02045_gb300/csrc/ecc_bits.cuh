@@ -387,6 +387,10 @@ __device__ void bits_span(const BitsImg& im, const BitsGeo& geo, int64_t tx, int
       g1w[my * kBitsG1Rec + 3 + i] = G1[0][i];
     }
     __syncthreads();
+    // the change evaluation, where a lane of the warp deposits (never in the
+    // collar warp or on a priming plane); warp-uniform, so the shuffles in it
+    // see the whole warp
+    if (__any_sync(FULL, z >= z0 && dep != 0u)) {
     uint32_t G01dn[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) G01dn[i] = g0[dn * kBitsG0Rec + i];
@@ -416,10 +420,7 @@ __device__ void bits_span(const BitsImg& im, const BitsGeo& geo, int64_t tx, int
       am[0][dx + 1] = ~Gdn1[1 - dx];  // neighbour (-1,-1,dx): delta (1,+1,-dx) of row br-1
       am[2][dx + 1] = ~Gup1[1 - dx];  // neighbour (-1,+1,dx): delta (1,-1,-dx) of row br+1
     }
-#pragma unroll
-    for (int i = 0; i < 3; ++i) Gp[i] = G1[1][i];
 
-    // (warp-uniform in the collar warp, whose lanes all have dep = 0)
     if (z >= z0 && dep) {
       // b(dz, dy, dx): after-bits (V) or their complement (T)
       auto b = [&](int dz, int dy, int dx) -> uint32_t {
@@ -558,6 +559,9 @@ __device__ void bits_span(const BitsImg& im, const BitsGeo& geo, int64_t tx, int
         deposit(v, N - 13);
       }
     }
+    }  // any lane deposits
+#pragma unroll
+    for (int i = 0; i < 3; ++i) Gp[i] = G1[1][i];
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
       Pz[k] = Pn[k];

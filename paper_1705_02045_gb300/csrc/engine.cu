@@ -141,12 +141,15 @@ int enqueue_int(ecc_handle* h, const void* d_img, int64_t row_pitch, const Shape
                 int64_t bins, long long* d_vcec, long long* d_curve, cudaStream_t stream,
                 const int64_t* chunk_end, const cudaEvent_t* chunk_ev, int n_chunks) {
   cudaError_t e;
-  if (!(d_vcec == h->clean_vcec && bins <= h->clean_bins)) {
+  // entries of d_vcec known to be zero; the buffer counts as dirty until this
+  // call has enqueued a launch that leaves it clean (an early error return
+  // after a partial launch sequence then forces the next call to clear it)
+  int64_t clean = d_vcec == h->clean_vcec ? h->clean_bins : 0;
+  h->clean_vcec = nullptr;
+  if (bins > clean) {
     if ((e = cudaMemsetAsync(d_vcec, 0, sizeof(long long) * bins, stream)))
       return cuda_err(h, e, "memset vcec");
-    if (h->clean_vcec != d_vcec) h->clean_bins = 0;
-    h->clean_vcec = d_vcec;
-    h->clean_bins = std::max(h->clean_bins, bins);
+    clean = bins;
   }
   if (s.voxels > 0) {
     LocalArgs a;
@@ -229,11 +232,10 @@ int enqueue_int(ecc_handle* h, const void* d_img, int64_t row_pitch, const Shape
     }
     if (fused) {
       h->clean_vcec = d_vcec;
-      h->clean_bins = std::max(h->clean_bins, bins);
+      h->clean_bins = clean;
       return ECC_OK;
     }
   }
-  h->clean_vcec = nullptr;
   int64_t cnt = 0;
   e = launch_scan(d_vcec, d_curve, bins, stream, &cnt);
   h->launches += cnt;

@@ -205,10 +205,18 @@ int enqueue_int(ecc_handle* h, const void* d_img, int64_t row_pitch, const Shape
       a.fused_curve = d_curve;
       a.done = h->done.as<unsigned int>();
     }
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // profiling events: destroyed on every return that does not hand them
+    // to the handle's record
+    struct EventPair {
+      cudaEvent_t a = nullptr, b = nullptr;
+      ~EventPair() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+      }
+    } prof;
     if (h->prof_on) {
-      if ((e = cudaEventCreate(&ev0)) || (e = cudaEventCreate(&ev1)) ||
-          (e = cudaEventRecord(ev0, stream)))
+      if ((e = cudaEventCreate(&prof.a)) || (e = cudaEventCreate(&prof.b)) ||
+          (e = cudaEventRecord(prof.a, stream)))
         return cuda_err(h, e, "profiling event");
     }
     const int K = n_chunks > 0 ? n_chunks : 1;
@@ -227,8 +235,9 @@ int enqueue_int(ecc_handle* h, const void* d_img, int64_t row_pitch, const Shape
       }
     }
     if (h->prof_on) {
-      if ((e = cudaEventRecord(ev1, stream))) return cuda_err(h, e, "profiling event");
-      h->prof_events.emplace_back(ev0, ev1);
+      if ((e = cudaEventRecord(prof.b, stream))) return cuda_err(h, e, "profiling event");
+      h->prof_events.emplace_back(prof.a, prof.b);
+      prof.a = prof.b = nullptr;
     }
     if (fused) {
       h->clean_vcec = d_vcec;

@@ -89,7 +89,10 @@ int tune_bits(ecc_handle* h, const LocalArgs& base, TuneChoice* best) {
   const int64_t planes = base.w_hi - base.w_lo;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e;
-  if ((e = cudaEventCreate(&e0)) || (e = cudaEventCreate(&e1))) return cuda_err(h, e, "tuner");
+  if ((e = cudaEventCreate(&e0)) || (e = cudaEventCreate(&e1))) {
+    if (e0) cudaEventDestroy(e0);
+    return cuda_err(h, e, "tuner");
+  }
   best->ms = 1e30f;
   best->warps = 0;
   best->zc = 0;

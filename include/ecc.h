@@ -112,8 +112,9 @@ int ecc_create(const ecc_config* cfg, ecc_handle** out);
  * a no-op. Pending requests are cancelled. */
 void ecc_destroy(ecc_handle* h);
 
-/* Message of the handle's last error ("" if none); valid until the next call
- * on the handle. h may be NULL for errors of ecc_create. */
+/* Message of the last error of this thread's calls on the handle ("" if
+ * none); valid until this thread's next call on the handle. h may be NULL
+ * for errors of ecc_create (also per thread). */
 const char* ecc_last_error(const ecc_handle* h);
 
 /* Frees the arrays of a result the library allocated; safe on zeroed or

@@ -648,7 +648,6 @@ struct Server {
   // the streamed request in progress (one at a time) and its streams
   SlabJob* job = nullptr;
   cudaStream_t job_stream = nullptr, job_copy = nullptr;
-  std::string err;
 };
 
 namespace {
@@ -1102,7 +1101,7 @@ int ecc_compute_batch(ecc_handle* h, int n, const ecc_image* images, ecc_result*
   if (!h) return ECC_ERR_ARG;
   try {
     std::lock_guard<std::mutex> lk(h->api_mu);
-    h->err.clear();
+    clear_err(h);
     if (n < 0 || (n > 0 && (!images || !outs))) return set_err(h, ECC_ERR_ARG, "bad batch");
     cudaError_t e = cudaSetDevice(h->device);
     if (e) return cuda_err(h, e, "set device");
@@ -1207,7 +1206,7 @@ int ecc_submit(ecc_handle* h, const void* image, const int64_t* dims, int ndim, 
     Shape s;
     {
       std::lock_guard<std::mutex> lk(h->api_mu);
-      h->err.clear();
+      clear_err(h);
       if (!req_id) return set_err(h, ECC_ERR_ARG, "req_id is NULL");
       int rc = validate_shape(h, dims, ndim, &s);
       if (rc) return rc;

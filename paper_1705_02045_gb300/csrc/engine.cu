@@ -16,6 +16,11 @@ namespace ecc {
 
 cudaError_t launch_local_generic(const LocalArgs& a, int num_sms, int64_t* launches);
 
+namespace {
+thread_local const ecc_handle* tl_err_h = nullptr;
+thread_local std::string tl_err;
+}  // namespace
+
 int set_err(ecc_handle* h, int code, const char* fmt, ...) {
   if (h) {
     char buf[512];
@@ -23,10 +28,17 @@ int set_err(ecc_handle* h, int code, const char* fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(buf, sizeof buf, fmt, ap);
     va_end(ap);
-    h->err = buf;
+    tl_err_h = h;
+    tl_err = buf;
   }
   return code;
 }
+
+void clear_err(const ecc_handle* h) {
+  if (tl_err_h == h) tl_err.clear();
+}
+
+const char* last_err(const ecc_handle* h) { return tl_err_h == h ? tl_err.c_str() : ""; }
 
 int cuda_err(ecc_handle* h, cudaError_t e, const char* what) {
   if (e == cudaSuccess) return ECC_OK;
@@ -384,7 +396,7 @@ void ecc_config_default(ecc_config* c) {
   c->tuner_cache = nullptr;
 }
 
-static std::string g_create_err;
+static thread_local std::string g_create_err;
 
 int ecc_create(const ecc_config* cfg, ecc_handle** out) {
   if (!out) return ECC_ERR_ARG;
@@ -475,7 +487,7 @@ void ecc_destroy(ecc_handle* h) {
 }
 
 const char* ecc_last_error(const ecc_handle* h) {
-  return h ? h->err.c_str() : g_create_err.c_str();
+  return h ? last_err(h) : g_create_err.c_str();
 }
 
 void ecc_result_free(ecc_result* r) {
@@ -498,7 +510,7 @@ int ecc_compute(ecc_handle* h, const void* image, const int64_t* dims, int ndim,
   if (!h) return ECC_ERR_ARG;
   try {
     std::lock_guard<std::mutex> lk(h->api_mu);
-    h->err.clear();
+    clear_err(h);
     if (!out) return set_err(h, ECC_ERR_ARG, "out is NULL");
     std::memset(out, 0, sizeof *out);
     out->owned = 1;
@@ -613,7 +625,7 @@ int ecc_compute_device(ecc_handle* h, const void* d_image, const int64_t* dims, 
   if (!h) return ECC_ERR_ARG;
   try {
     std::lock_guard<std::mutex> lk(h->api_mu);
-    h->err.clear();
+    clear_err(h);
     Shape s;
     int rc = validate_shape(h, dims, ndim, &s);
     if (rc) return rc;
@@ -642,7 +654,7 @@ int ecc_compute_quantized(ecc_handle* h, const float* image, const int64_t* dims
   if (!h) return ECC_ERR_ARG;
   try {
     std::lock_guard<std::mutex> lk(h->api_mu);
-    h->err.clear();
+    clear_err(h);
     if (!out) return set_err(h, ECC_ERR_ARG, "out is NULL");
     std::memset(out, 0, sizeof *out);
     out->owned = 1;

@@ -83,7 +83,6 @@ struct ecc_handle {
   ecc::Tuner* tuner = nullptr;         // launch-shape tuner (tuner_cache set or ECC_TUNE)
   cudaStream_t stream = nullptr;       // compute
   cudaStream_t copy_stream = nullptr;  // host <-> device
-  std::string err;
   std::mutex api_mu;                    // serialises the blocking entry points
   std::atomic<int64_t> launches{0};
   int64_t launch_tmp = 0;
@@ -111,7 +110,12 @@ struct ecc_handle {
 
 namespace ecc {
 
+// Error messages are kept per thread (the request loop's scheduler thread
+// reports errors while the caller's threads use the handle): set_err records
+// the message for (this thread, h), clear_err forgets it, last_err reads it.
 int set_err(ecc_handle* h, int code, const char* fmt, ...);
+void clear_err(const ecc_handle* h);
+const char* last_err(const ecc_handle* h);
 int cuda_err(ecc_handle* h, cudaError_t e, const char* what);
 int validate_shape(ecc_handle* h, const int64_t* dims, int ndim, Shape* s);
 int64_t default_bins(const ecc_handle* h, int dtype);

@@ -120,7 +120,7 @@ int ecc_stream_begin(ecc_handle* h, const int64_t* dims, int ndim, ecc_dtype dty
   if (!h) return ECC_ERR_ARG;
   try {
     std::lock_guard<std::mutex> lk(h->api_mu);
-    h->err.clear();
+    clear_err(h);
     if (!out) return set_err(h, ECC_ERR_ARG, "out is NULL");
     *out = nullptr;
     Shape s;
@@ -196,7 +196,7 @@ int ecc_stream_push_slab(ecc_stream* st, const void* host_planes, int64_t z0, in
   ecc_handle* h = st->h;
   try {
     std::lock_guard<std::mutex> lk(h->api_mu);
-    h->err.clear();
+    clear_err(h);
     if (st->failed) return set_err(h, ECC_ERR_STATE, "stream failed earlier");
     if (z0 != st->next_z)
       return set_err(h, ECC_ERR_STATE, "expected plane %lld, got %lld", (long long)st->next_z,
@@ -278,7 +278,7 @@ int ecc_stream_finish(ecc_stream* st, ecc_result* out) {
   int rc = ECC_OK;
   try {
     std::unique_lock<std::mutex> lk(h->api_mu);
-    h->err.clear();
+    clear_err(h);
     if (!out) {
       rc = set_err(h, ECC_ERR_ARG, "out is NULL");
     } else if (st->failed) {
@@ -464,9 +464,7 @@ int ecc_stream_file(ecc_handle* h, const char* path, int64_t offset, const int64
   if (rc == ECC_OK) {
     rc = ecc_stream_finish(st, out);
   } else {
-    const std::string msg = h->err;
-    ecc_stream_abort(st);
-    h->err = msg;
+    ecc_stream_abort(st);  // keeps this thread's message
   }
   for (int j = 0; j < 2; ++j)
     if (buf[j]) cudaFreeHost(buf[j]);

@@ -389,3 +389,43 @@ def test_stream_file_errors(lib, tmp_path):
                               oracle.ecc_int(img, 256, "V"))
     finally:
         ecc.ecc_destroy(h)
+
+
+def test_serve_concurrent_submitters(lib):
+    """Four client threads submit and poll at once (ecc_submit / ecc_poll may be
+    called concurrently); every result is the oracle's, and a bad request in
+    one thread reports its own error to that thread."""
+    import threading
+    imgs = _mixed_images(48, S + 80, max2d=120, max3d=32)
+    h = ecc.ecc_create(device=0, bins=16384)
+    results, errors = {}, []
+
+    def client(k):
+        try:
+            mine = imgs[k::4]
+            ids = [ecc.ecc_submit(h, img) for img, _ in mine]
+            for (img, _), rid in zip(mine, ids):
+                st, curve = ecc.ecc_poll(h, rid, timeout_us=120_000_000)
+                results[id(img)] = (img, curve)
+            if k == 0:
+                try:
+                    ecc.ecc_submit(h, np.zeros((3, 3), np.float32))
+                    errors.append("no error")
+                except ecc.EccError as e:
+                    if e.status != ecc.ECC_ERR_DTYPE or "ECC_U8" not in str(e):
+                        errors.append(f"unexpected {e.status} {e}")
+        except Exception as e:  # pragma: no cover - reported below
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=client, args=(k,)) for k in range(4)]
+    try:
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+    finally:
+        ecc.ecc_destroy(h)
+    assert not errors, errors
+    assert len(results) == len(imgs)
+    for img, curve in results.values():
+        assert np.array_equal(curve, oracle.ecc_int(img, 16384, "V"))

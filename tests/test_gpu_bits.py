@@ -289,3 +289,25 @@ def test_fused_scan_interleaved_with_other_paths():
     finally:
         ecc.ecc_destroy(h)
         ecc.ecc_destroy(h16)
+
+
+def test_1d_longer_than_2_pow_31():
+    """A 1D uint8 image of 2^31 + 12345 voxels (64-bit indexing throughout):
+    chi(K_t) is the number of runs of {f <= t}, i.e. the voxels <= t minus the
+    adjacent pairs whose larger value is <= t (the run count the oracle is
+    pinned to in 1D)."""
+    import torch
+    n = (1 << 31) + 12345
+    g = torch.Generator(device="cuda").manual_seed(synth.SEED_BASE + 90)
+    d = torch.randint(0, 256, (n,), generator=g, device="cuda", dtype=torch.int16).to(torch.uint8)
+    h = ecc.ecc_create(device=0)
+    try:
+        got = ecc.ecc_compute(h, d)
+    finally:
+        ecc.ecc_destroy(h)
+    c1 = torch.bincount(d.long(), minlength=256)
+    pair_max = torch.maximum(d[1:], d[:-1]).long()
+    c2 = torch.bincount(pair_max, minlength=256)
+    want = (torch.cumsum(c1, 0) - torch.cumsum(c2, 0)).cpu().numpy()
+    assert np.array_equal(got, want)
+    assert got[-1] == 1

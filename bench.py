@@ -348,6 +348,7 @@ def workload_stream(args):
     ecc.ecc_destroy(h)
     # resident
     d = hu.cuda()
+    torch.cuda.synchronize()
     h = ecc.ecc_create(device=0, bins=16384)
     c = torch.empty(16384, dtype=torch.int64, device="cuda")
     st = torch.cuda.Stream()
@@ -406,6 +407,7 @@ def workload_f32q(args):
     shape = tuple(int(s) for s in args.volume.split(","))
     nvox = int(np.prod(shape))
     d = synth.grf_f32_torch(shape, 3.0, synth.SEED_BASE + 4).contiguous()
+    torch.cuda.synchronize()
     lo, hi, bins = float(d.min()), float(d.max()), 16384
     h = ecc.ecc_create(device=0)
     curve = ecc.ecc_compute_quantized(h, d, lo, hi, bins)
@@ -567,6 +569,7 @@ def workload_f32(args):
     shape = tuple(int(s) for s in args.volume.split(","))
     nvox = int(np.prod(shape))
     d = synth.grf_f32_torch(shape, 3.0, synth.SEED_BASE + 4).contiguous()
+    torch.cuda.synchronize()
     h = ecc.ecc_create(device=0)
     t, chi = ecc.ecc_compute(h, d)
     times = []

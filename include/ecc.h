@@ -25,7 +25,10 @@
  *
  * Pointers: an "image" argument may be a host pointer (pageable or pinned) or
  * a device pointer of the handle's device; the library tells them apart with
- * cudaPointerGetAttributes. The caller keeps ownership of every argument.
+ * cudaPointerGetAttributes. The caller keeps ownership of every argument. The
+ * blocking calls run on streams that synchronise with the legacy default
+ * stream: a device image written there is complete before it is read; one
+ * written on another stream must be synchronised by the caller first.
  * Every call returns an int status (ECC_OK or a negative ECC_ERR_*); no C++
  * exception ever crosses this boundary. ecc_last_error() gives a message.
  *

@@ -341,14 +341,18 @@ cudaError_t grids_for(int num_sms, int* grid_b, int* grid_g) {
   return cudaSuccess;
 }
 
-int slot_init(ecc_handle* h, Slot& sl) {
+// blocking: the slot's stream synchronises with the legacy default stream
+// (ecc_compute_batch, whose device images may come from there); the serving
+// slots take host images only and stay non-blocking.
+int slot_init(ecc_handle* h, Slot& sl, bool blocking) {
   cudaError_t e;
   int gb = 0, gg = 0;
   e = h->cfg.convention == kConvT ? grids_for<kConvT>(h->num_sms, &gb, &gg)
                                   : grids_for<kConvV>(h->num_sms, &gb, &gg);
   if (e) return cuda_err(h, e, "batch occupancy");
   sl.L = desc_layout(gb, gg);
-  if ((e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking)) ||
+  if ((e = cudaStreamCreateWithFlags(&sl.stream,
+                                     blocking ? cudaStreamDefault : cudaStreamNonBlocking)) ||
       (e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming)) ||
       (e = cudaEventCreate(&sl.t0)) || (e = cudaEventCreate(&sl.t1)) ||
       (e = sl.desc.ensure(sl.L.total)) || (e = cudaMallocHost(&sl.h_desc, sl.L.total)))
@@ -1035,7 +1039,7 @@ int server_start(ecc_handle* h) {
   }
   sv->eng.slots.resize(2);
   for (Slot& sl : sv->eng.slots) {
-    int rc = slot_init(h, sl);
+    int rc = slot_init(h, sl, false);
     if (rc) {
       for (Slot& s2 : sv->eng.slots) slot_free(s2);
       delete sv;
@@ -1112,7 +1116,7 @@ int ecc_compute_batch(ecc_handle* h, int n, const ecc_image* images, ecc_result*
     if (!h->batch) {
       h->batch = new BatchEngine();
       h->batch->slots.resize(1);
-      int rc = slot_init(h, h->batch->slots[0]);
+      int rc = slot_init(h, h->batch->slots[0], true);
       if (rc) {
         slot_free(h->batch->slots[0]);
         delete h->batch;

@@ -444,7 +444,10 @@ int ecc_create(const ecc_config* cfg, ecc_handle** out) {
   }
   if ((e = cudaSetDevice(h->device)) ||
       (e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device)) ||
-      (e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) ||
+      // the compute stream of the blocking calls synchronises with the legacy
+      // default stream, so a device image written there (as by PyTorch's
+      // default stream) is complete before the kernels read it
+      (e = cudaStreamCreate(&h->stream)) ||
       (e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking)) ||
       (e = h->errw.ensure(sizeof(int))) ||
       (e = cudaMemset(h->errw.p, 0, sizeof(int))) ||

@@ -95,7 +95,10 @@ __device__ __forceinline__ void bits_blocks(const BitsImg& im, const BitsGeo& ge
     __shared__ int last;
     __threadfence();  // this thread's VCEC atomics before the block's ticket
     __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(im.done, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) {
+      __threadfence();
+      last = atomicAdd(im.done, 1u) == gridDim.x - 1;
+    }
     __syncthreads();
     if (last) {
       __threadfence();

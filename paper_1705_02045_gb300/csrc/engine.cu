@@ -285,13 +285,11 @@ int wait_event(ecc_handle* h, cudaEvent_t ev, int64_t timeout_us) {
 
 // Bounded stream synchronisation through an event (5 minutes).
 static int sync_stream(ecc_handle* h, cudaStream_t s) {
-  cudaEvent_t ev;
-  cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-  if (e != cudaSuccess) return cuda_err(h, e, "event create");
-  e = cudaEventRecord(ev, s);
-  int rc = e == cudaSuccess ? wait_event(h, ev, 300LL * 1000 * 1000) : cuda_err(h, e, "record");
-  cudaEventDestroy(ev);
-  return rc;
+  cudaError_t e = cudaSuccess;
+  if (!h->sync_ev && (e = cudaEventCreateWithFlags(&h->sync_ev, cudaEventDisableTiming)))
+    return cuda_err(h, e, "event create");
+  e = cudaEventRecord(h->sync_ev, s);
+  return e == cudaSuccess ? wait_event(h, h->sync_ev, 300LL * 1000 * 1000) : cuda_err(h, e, "record");
 }
 
 static int read_err_word(ecc_handle* h, cudaStream_t s, int* word) {
@@ -483,6 +481,7 @@ void ecc_destroy(ecc_handle* h) {
   if (h->h_err) cudaFreeHost(h->h_err);
   if (h->h_curve) cudaFreeHost(h->h_curve);
   for (cudaEvent_t ev : h->up_ev) cudaEventDestroy(ev);
+  if (h->sync_ev) cudaEventDestroy(h->sync_ev);
   if (h->up_free) cudaEventDestroy(h->up_free);
   if (h->stream) cudaStreamDestroy(h->stream);
   if (h->copy_stream) cudaStreamDestroy(h->copy_stream);

@@ -96,6 +96,7 @@ struct ecc_handle {
   int* h_err = nullptr;                 // pinned scalar for error readback
   std::vector<cudaEvent_t> up_ev;       // chunked host-image upload (ecc_compute)
   cudaEvent_t up_free = nullptr;        // the image buffer's previous readers are done
+  cudaEvent_t sync_ev = nullptr;        // bounded waits of the blocking calls
   int64_t* h_curve = nullptr;           // pinned staging of integer curves
   size_t h_curve_cap = 0;               // entries of h_curve
 

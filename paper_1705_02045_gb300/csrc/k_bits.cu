@@ -2,6 +2,7 @@
 // a persistent grid walks the tiles of one image, each block keeping a
 // private histogram that it adds to the int64 VCEC at the end.
 #include "ecc_bits.cuh"
+#include "occupancy.h"
 
 #include <algorithm>
 #include <cstdlib>
@@ -122,10 +123,9 @@ cudaError_t launch_t(const BitsImg& im, int W, int64_t zc, int grid_req, int num
   const size_t words = (size_t)threads * (pl_rec + kBitsG0Rec + 2 * kBitsG1Rec);
   const size_t smem = words * 4 + (HM == kBitsSmem ? sizeof(int) * (size_t)im.bins : 0);
   auto kern = k_bits3<NB, CONV, HM>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e) return e;
   int per_sm = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem))) return e;
+  cudaError_t e = blocks_per_sm(kern, threads, smem, &per_sm);
+  if (e) return e;
   if (per_sm < 1) return cudaErrorNotSupported;
   const int64_t grid_cap = (int64_t)per_sm * num_sms;
   const int64_t wn = im.w_hi - im.w_lo;

@@ -10,6 +10,7 @@
 // Sec. 3 ("Processing one Chunk"). Outside voxels are +inf (Sec. 4,
 // limitations: the second collar of infinite voxels), here by a bounds test.
 #include "ecc_tile.cuh"
+#include "occupancy.h"
 
 #include <algorithm>
 #include <type_traits>
@@ -254,11 +255,8 @@ cudaError_t launch_typed(const LocalArgs& a, int num_sms, int64_t* launches) {
   if (a.view == 3) {
     const size_t smem = 4 * kT3PL * 4 + 256 + hist_bytes;
     auto kern = k_local3<T, CONV, MODE>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+    cudaError_t e = blocks_per_sm(kern, kThreads, smem, &per_sm);
     if (e != cudaSuccess) return e;
     const int64_t tiles_x = (a.n[2] + kT3X - 1) / kT3X, tiles_y = (a.n[1] + kT3Y - 1) / kT3Y;
     const int64_t grid_cap = (int64_t)std::max(per_sm, 1) * num_sms;
@@ -277,11 +275,8 @@ cudaError_t launch_typed(const LocalArgs& a, int num_sms, int64_t* launches) {
   }
   const size_t smem = 4 * k4PL * 4 + 256 + hist_bytes;
   auto kern = k_local4<T, CONV, MODE>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+  cudaError_t e = blocks_per_sm(kern, kThreads, smem, &per_sm);
   if (e != cudaSuccess) return e;
   const int64_t tiles_x = (a.n[3] + k4TX - 1) / k4TX, tiles_y = (a.n[2] + k4TY - 1) / k4TY,
                 tiles_z = (a.n[1] + k4TZ - 1) / k4TZ;

@@ -243,7 +243,7 @@ struct Slot {
   DevBuf arena;
   unsigned char* h_arena = nullptr;
   size_t h_arena_cap = 0;
-  DevBuf staging;  // pitched copies of host / unaligned images
+  DevBuf staging;  // device copies of the batch's host images (dense rows)
   cudaGraphExec_t exec_small = nullptr, exec_large = nullptr;
   cudaEvent_t done = nullptr;
   cudaEvent_t t0 = nullptr, t1 = nullptr;  // around the graph, for the online tuner
@@ -1150,13 +1150,10 @@ int ecc_compute_batch(ecc_handle* h, int n, const ecc_image* images, ecc_result*
       sp.d_img = im.data;
       sp.row_pitch = 0;
       if (s.voxels == 0) continue;
-      // host images, and device images whose rows the bit-sliced kernel
-      // cannot load, are copied into the slot's staging buffer
-      const int64_t dense = (int64_t)dtype_bytes(im.dtype) * sp.n[2];
+      // host images are copied into the slot's staging buffer; device
+      // images are read in place (the kernels take rows at any alignment)
       const int64_t pitch = staged_pitch(h, im.dtype, bins, sp.n[2]);
       const bool dev = is_device_ptr(h, im.data);
-      const bool aligned = (reinterpret_cast<uintptr_t>(im.data) & 15u) == 0 && dense % 16 == 0;
-      (void)aligned;
       if (!dev) {
         sp.row_pitch = pitch;
         stage_off[i] = staged;

@@ -25,11 +25,11 @@
 //
 // Layout: a row group of L lanes covers a whole row (L = the power of two
 // >= nx / 32), or, for rows wider than 1024, a warp covers 1024 voxels of
-// which the middle 960 are its own (lanes 0 and 31 supply the x-collar). The
-// warps of a block stack consecutive rows (the first and the last row are the
-// y-collar); the block marches along z. y-neighbour planes and the exported
-// comparison words go through shared memory, x-neighbour bits through warp
-// shuffles.
+// which the middle 960 are its own (lanes 0 and 31 supply the x-collar). A
+// block holds consecutive rows (the first and the last row are the y-collar,
+// both in its first warp) and marches along z over a span of planes.
+// y-neighbour planes and the exported comparison words go through shared
+// memory, x-neighbour bits through warp shuffles.
 #pragma once
 
 #include <cstdint>
@@ -50,7 +50,7 @@ struct BitsGeo {
 struct BitsImg {
   const unsigned char* img;  // plane w_mem_lo of the image
   int64_t n[3];              // z, y, x
-  int64_t row_pitch;         // bytes between rows (multiple of 16)
+  int64_t row_pitch;         // bytes between rows (rows may start at any byte)
   int64_t w_lo, w_hi;        // planes processed
   int64_t w_mem_lo, w_mem_hi;  // planes resident at img
   int64_t bins;

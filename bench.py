@@ -674,9 +674,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--batch-images", type=int, default=512,
+    ap.add_argument("--batch-images", type=int, default=1024,
                     help="images of the mixed request stream in the batched comparison")
-    ap.add_argument("--serve-requests", type=int, default=1024,
+    ap.add_argument("--serve-requests", type=int, default=4096,
                     help="requests of the served Poisson stream (0 = skip)")
     ap.add_argument("--profile-launches", type=int, default=0,
                     help="only run this many ecc_compute_device launches (for ncu) and exit")

@@ -11,20 +11,20 @@ import numpy as np
 
 
 def _task(args):
-    path, shape, dtype, bins, lo, hi = args
+    path, shape, dtype, bins, lo, hi, conv = args
     import oracle
     img = np.memmap(path, dtype=dtype, mode="r", shape=shape)
-    return oracle.vcec_int_zrange(img, bins, lo, hi, "V")
+    return oracle.vcec_int_zrange(img, bins, lo, hi, conv)
 
 
 def ecc_int_parallel(path, shape, dtype, bins: int, planes_per_task: int = 4,
-                     procs: int | None = None) -> np.ndarray:
+                     procs: int | None = None, conv: str = "V") -> np.ndarray:
     """Curve of the raw C-order image in `path` by the oracle, one spawned
     process per host core."""
     procs = procs or max(1, os.cpu_count() or 1)
     n0 = shape[0]
     tasks = [(str(path), tuple(shape), np.dtype(dtype).str, bins, lo,
-              min(lo + planes_per_task, n0 + 1))
+              min(lo + planes_per_task, n0 + 1), conv)
              for lo in range(0, n0 + 1, planes_per_task)]
     total = np.zeros(bins, dtype=np.int64)
     with mp.get_context("spawn").Pool(procs) as pool:

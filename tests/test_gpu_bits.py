@@ -154,16 +154,20 @@ def test_bits_stream_slabs():
     assert np.array_equal(got, oracle.ecc_int(img, 16384, "V"))
 
 
-def test_bits_full_size_512_cube():
-    """The 512^3 smoothed uint8 benchmark image: bit-sliced == generic, and the
-    oracle on a 64-plane slab of it (cells with z in [0, 64))."""
+@pytest.mark.parametrize("conv", [0, 1])
+def test_bits_full_size_512_cube(tmp_path, conv):
+    """The 512^3 smoothed uint8 benchmark image: bit-sliced == generic == the
+    oracle over the whole image (one process per host core, 16-plane chunks)."""
+    import oracle_pool
     img = synth.smooth_u8((512, 512, 512), 4.0, synth.SEED_BASE + 1)
-    got, gen = _both(img, 256, 0)
+    got, gen = _both(img, 256, conv)
     assert np.array_equal(got, gen)
     assert got[-1] == 1
-    sub = np.ascontiguousarray(img[:64])
-    g_sub, _ = _both(sub, 256, 0)
-    assert np.array_equal(g_sub, oracle.ecc_int(sub, 256, "V"))
+    path = tmp_path / "cube.raw"
+    img.tofile(path)
+    want = oracle_pool.ecc_int_parallel(path, img.shape, np.uint8, 256, planes_per_task=16,
+                                        conv="V" if conv == 0 else "T")
+    assert np.array_equal(got, want)
 
 
 def test_tuner_picks_and_caches_a_launch_shape(tmp_path):

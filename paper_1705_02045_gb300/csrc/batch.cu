@@ -25,6 +25,7 @@
 #include "ecc_tile.cuh"
 #include "engine.h"
 
+#include <atomic>
 #include <chrono>
 #include <cstdlib>
 #include <cstring>
@@ -652,6 +653,7 @@ struct Server {
   // the streamed request in progress (one at a time) and its streams
   SlabJob* job = nullptr;
   cudaStream_t job_stream = nullptr, job_copy = nullptr;
+  std::atomic<uint64_t> submitted{0};  // requests queued so far (wakes the poller)
 };
 
 namespace {
@@ -1014,10 +1016,20 @@ void serve_loop(ecc_handle* h) {
     bool busy = sv->job != nullptr;
     for (int s = 0; s < nslots; ++s) busy = busy || !sv->in_flight[s].empty();
     if (busy) {
-      // work on the GPU: poll again at once (a timed wait costs the timer
-      // slack, ~50 us, on every completion)
+      // work on the GPU: poll for a finished batch or a new request without
+      // holding the lock, so submitting threads get it at once (a timed wait
+      // would cost the timer slack, ~50 us, on every completion). in_flight
+      // and job are only changed by this thread.
+      const uint64_t seen = sv->submitted.load(std::memory_order_acquire);
       lk.unlock();
-      std::this_thread::yield();
+      for (int spin = 0; spin < 256 && !sv->job; ++spin) {
+        bool finished = false;
+        for (int s = 0; s < nslots && !finished; ++s)
+          finished = !sv->in_flight[s].empty() &&
+                     cudaEventQuery(sv->eng.slots[s].done) != cudaErrorNotReady;
+        if (finished || sv->submitted.load(std::memory_order_acquire) != seen) break;
+        std::this_thread::yield();
+      }
       lk.lock();
     } else {
       sv->cv.wait_for(lk, std::chrono::milliseconds(5));
@@ -1294,6 +1306,7 @@ int ecc_submit(ecc_handle* h, const void* image, const int64_t* dims, int ndim, 
       if (r->state == Request::kQueuedHost && !r->streamed) admit(h, sv, r);
       sv->queue.push_back(r);
       *req_id = r->id;
+      sv->submitted.fetch_add(1, std::memory_order_release);
     }
     sv->cv.notify_all();
     return ECC_OK;

@@ -58,12 +58,15 @@ struct BItem {
 struct BHeader {
   int n_images;
   int n_items_bits, n_items_gen;
+  int n_chunks_b;  // chunks of the bit-sliced work list (runs of items of about equal cost)
+  int next_b;      // next chunk to claim; 0 in every uploaded descriptor
 };
 
 constexpr int kMaxBatch = 1024;
 constexpr int64_t kSmallBins = 256;
 constexpr int kBatchBitsWarps = 8;
 constexpr int kBatchPlRec = 17;  // odd and >= 16 + 1 planes
+constexpr int kGrabPerBlock = 4;  // bit-sliced work-list chunks per persistent block
 
 namespace {
 
@@ -77,13 +80,13 @@ DescLayout desc_layout(int grid_b, int grid_g) {
   DescLayout L;
   L.grid_b = grid_b;
   L.grid_g = grid_g;
-  L.item_cap_b = kMaxBatch + grid_b + 1;
+  L.item_cap_b = kMaxBatch + grid_b * kGrabPerBlock + 1;
   L.item_cap_g = kMaxBatch + grid_g + 1;
   size_t o = 0;
   L.hdr = o; o += up(sizeof(BHeader));
   L.imgs = o; o += up(sizeof(BImage) * kMaxBatch);
   L.items_b = o; o += up(sizeof(BItem) * L.item_cap_b);
-  L.starts_b = o; o += up(sizeof(int) * (grid_b + 1));
+  L.starts_b = o; o += up(sizeof(int) * (grid_b * kGrabPerBlock + 1));
   L.items_g = o; o += up(sizeof(BItem) * L.item_cap_g);
   L.starts_g = o; o += up(sizeof(int) * (grid_g + 1));
   L.total = o;
@@ -165,46 +168,69 @@ __device__ void bits_item(const BImage& im, const BItem& item, uint32_t* pl, uin
     bits_tile<NB, CONV, HM>(bi, im.geo, t, pl, g0, g1, kBatchPlRec, hist);
 }
 
+// Adds the block's shared histogram into the image's VCEC and clears it.
+__device__ __forceinline__ void flush_bits_hist(const BImage& im, int* hist) {
+  __syncthreads();
+  for (int64_t b = threadIdx.x; b < im.bins; b += blockDim.x) {
+    const int v = hist[b];
+    if (v) {
+      atomicAdd(reinterpret_cast<unsigned long long*>(im.vcec) + b,
+                (unsigned long long)(long long)v);
+      hist[b] = 0;
+    }
+  }
+  __syncthreads();
+}
+
+// Persistent blocks claim chunks of the work list in order through the
+// header's counter, so that a block whose chunks ran fast takes more of them.
+// A block's shared histogram is flushed when its next item belongs to
+// another image and after its last chunk.
 template <int CONV, int SMEM_BINS>
 __global__ void __launch_bounds__(32 * kBatchBitsWarps, 2)
-k_batch_bits(const unsigned char* __restrict__ desc, DescLayout L) {
+k_batch_bits(unsigned char* __restrict__ desc, DescLayout L) {
   extern __shared__ __align__(16) uint32_t sm[];
+  __shared__ int s_chunk;
   const int recs = 32 * kBatchBitsWarps;
   uint32_t* pl = sm;
   uint32_t* g0 = pl + recs * kBatchPlRec;
   uint32_t* g1 = g0 + recs * kBitsG0Rec;
   int* hist = reinterpret_cast<int*>(g1 + 2 * recs * kBitsG1Rec);
+  BHeader* hdr = reinterpret_cast<BHeader*>(desc + L.hdr);
   const BImage* imgs = reinterpret_cast<const BImage*>(desc + L.imgs);
   const BItem* items = reinterpret_cast<const BItem*>(desc + L.items_b);
   const int* starts = reinterpret_cast<const int*>(desc + L.starts_b);
-  const int i0 = starts[blockIdx.x], i1 = starts[blockIdx.x + 1];
-  if (i0 >= i1) return;
+  const int n_chunks = hdr->n_chunks_b;
+  if (n_chunks <= 0) return;
   for (int b = threadIdx.x; b < SMEM_BINS; b += blockDim.x) hist[b] = 0;
-  __syncthreads();
-  for (int it = i0; it < i1; ++it) {
-    const BItem item = items[it];
-    const BImage& im = imgs[item.image];
-    const bool smem_hist = im.bins <= SMEM_BINS;
-    if (smem_hist) {
-      if (im.nb == 8) bits_item<CONV, 8, kBitsSmem>(im, item, pl, g0, g1, hist);
-      else if (im.nb == 14) bits_item<CONV, 14, kBitsSmem>(im, item, pl, g0, g1, hist);
-      else bits_item<CONV, 16, kBitsSmem>(im, item, pl, g0, g1, hist);
-      __syncthreads();
-      for (int64_t b = threadIdx.x; b < im.bins; b += blockDim.x) {
-        const int v = hist[b];
-        if (v) {
-          atomicAdd(reinterpret_cast<unsigned long long*>(im.vcec) + b,
-                    (unsigned long long)(long long)v);
-          hist[b] = 0;
-        }
+  int cur = -1;  // image whose counts sit in the shared histogram
+  for (;;) {
+    if (threadIdx.x == 0) s_chunk = atomicAdd(&hdr->next_b, 1);
+    __syncthreads();
+    const int c = s_chunk;
+    __syncthreads();
+    if (c >= n_chunks) break;
+    for (int it = starts[c]; it < starts[c + 1]; ++it) {
+      const BItem item = items[it];
+      const BImage& im = imgs[item.image];
+      const bool smem_hist = im.bins <= SMEM_BINS;
+      if (cur >= 0 && cur != item.image) {
+        flush_bits_hist(imgs[cur], hist);
+        cur = -1;
       }
-      __syncthreads();
-    } else {
-      if (im.nb == 8) bits_item<CONV, 8, kBitsGlobal>(im, item, pl, g0, g1, hist);
-      else if (im.nb == 14) bits_item<CONV, 14, kBitsGlobal>(im, item, pl, g0, g1, hist);
-      else bits_item<CONV, 16, kBitsGlobal>(im, item, pl, g0, g1, hist);
+      if (smem_hist) {
+        cur = item.image;
+        if (im.nb == 8) bits_item<CONV, 8, kBitsSmem>(im, item, pl, g0, g1, hist);
+        else if (im.nb == 14) bits_item<CONV, 14, kBitsSmem>(im, item, pl, g0, g1, hist);
+        else bits_item<CONV, 16, kBitsSmem>(im, item, pl, g0, g1, hist);
+      } else {
+        if (im.nb == 8) bits_item<CONV, 8, kBitsGlobal>(im, item, pl, g0, g1, hist);
+        else if (im.nb == 14) bits_item<CONV, 14, kBitsGlobal>(im, item, pl, g0, g1, hist);
+        else bits_item<CONV, 16, kBitsGlobal>(im, item, pl, g0, g1, hist);
+      }
     }
   }
+  if (cur >= 0) flush_bits_hist(imgs[cur], hist);
 }
 
 __global__ void k_batch_zero(const unsigned char* __restrict__ desc, DescLayout L) {
@@ -291,7 +317,7 @@ template <int CONV>
 cudaError_t capture_graph(Slot& sl, bool large, cudaGraphExec_t* out) {
   cudaError_t e;
   cudaGraph_t g = nullptr;
-  const unsigned char* d = sl.desc.as<unsigned char>();
+  unsigned char* d = sl.desc.as<unsigned char>();
   if ((e = cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal))) return e;
   k_batch_zero<<<kMaxBatch, 256, 0, sl.stream>>>(d, sl.L);
   if (large) {
@@ -529,12 +555,15 @@ int slot_run(ecc_handle* h, Slot& sl, BatchTune& tune, const std::vector<ImgSpec
   BItem* items_g = reinterpret_cast<BItem*>(sl.h_desc + sl.L.items_g);
   int* starts_b = reinterpret_cast<int*>(sl.h_desc + sl.L.starts_b);
   int* starts_g = reinterpret_cast<int*>(sl.h_desc + sl.L.starts_g);
-  const int nib = partition(ib, tb, cb, sl.L.grid_b, items_b, sl.L.item_cap_b, starts_b);
+  const int n_chunks = sl.L.grid_b * kGrabPerBlock;
+  const int nib = partition(ib, tb, cb, n_chunks, items_b, sl.L.item_cap_b, starts_b);
   const int nig = partition(ig, tg, cg, sl.L.grid_g, items_g, sl.L.item_cap_g, starts_g);
   if (nib < 0 || nig < 0) return set_err(h, ECC_ERR_CUDA, "work list overflow");
   hdr->n_images = n;
   hdr->n_items_bits = nib;
   hdr->n_items_gen = nig;
+  hdr->n_chunks_b = nib > 0 ? n_chunks : 0;
+  hdr->next_b = 0;
   if (wait_ev && (e = cudaStreamWaitEvent(sl.stream, wait_ev, 0))) return cuda_err(h, e, "wait");
   if ((e = cudaMemcpyAsync(sl.desc.p, sl.h_desc, sl.L.total, cudaMemcpyHostToDevice, sl.stream)))
     return cuda_err(h, e, "upload work list");

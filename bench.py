@@ -266,12 +266,15 @@ def bench_batched(h, reqs, stream):
             "gvox_s_per_image": vox / tp / 1e9, "identical": bool(same)}
 
 
-def bench_serving(h, reqs, rate_hz: float, seed: int):
+def bench_serving(h, reqs, rate_hz: float, seed: int, borrowed: bool = False):
     """Requests submitted at Poisson arrival times (rate_hz), polled to
     completion; latency = submit -> completion as recorded by the library.
     rate_hz = 0: all submitted at once (saturated). Request images are in
-    pinned host memory (as from a receive buffer registered with CUDA)."""
+    pinned host memory (as from a receive buffer registered with CUDA);
+    borrowed: ecc_submit_borrowed, which reads them in place instead of
+    copying each before it returns."""
     from paper_1705_02045_gb300 import ecc
+    submit = ecc.ecc_submit_borrowed if borrowed else ecc.ecc_submit
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate_hz, size=len(reqs)) if rate_hz > 0 else np.zeros(len(reqs))
     arrivals = np.cumsum(gaps)
@@ -283,7 +286,7 @@ def bench_serving(h, reqs, rate_hz: float, seed: int):
             dt = arrivals[i] - (time.perf_counter() - t0)
             if dt > 0:
                 time.sleep(dt)
-            ids[i] = ecc.ecc_submit(h, img)
+            ids[i] = submit(h, img)
 
     t0 = time.perf_counter()
     th = threading.Thread(target=submitter)
@@ -838,21 +841,27 @@ def main():
                 ecc.ecc_destroy(hb)
             if args.serve_requests > 0:
                 sreqs = [(torch.from_numpy(a).pin_memory(), b) for a, b in reqs[:args.serve_requests]]
-                hs = ecc.ecc_create(device=local)
-                try:
-                    sat = bench_serving(hs, sreqs, 0.0, synth.SEED_BASE + 4)
-                finally:
-                    ecc.ecc_destroy(hs)
-                rate = 0.8 * len(sreqs) / sat["wall_s"]
-                hs = ecc.ecc_create(device=local)
-                try:
-                    pois = bench_serving(hs, sreqs, rate, synth.SEED_BASE + 5)
-                finally:
-                    ecc.ecc_destroy(hs)
-                line["serving"] = {"poisson_0.8x": pois, "saturated": sat,
-                                   "workload": "mixed 2D/3D uint8 / 14-bit uint16 requests in pinned "
-                                               "host memory, smoothed fields sigma=2 "
-                                               "(synth.request_mix)"}
+                def serve_pair(borrowed):
+                    # saturated, then Poisson arrivals at 0.8x its throughput
+                    hs = ecc.ecc_create(device=local)
+                    try:
+                        sat = bench_serving(hs, sreqs, 0.0, synth.SEED_BASE + 4, borrowed)
+                    finally:
+                        ecc.ecc_destroy(hs)
+                    rate = 0.8 * len(sreqs) / sat["wall_s"]
+                    hs = ecc.ecc_create(device=local)
+                    try:
+                        pois = bench_serving(hs, sreqs, rate, synth.SEED_BASE + 5, borrowed)
+                    finally:
+                        ecc.ecc_destroy(hs)
+                    return {"poisson_0.8x": pois, "saturated": sat}
+
+                line["serving"] = dict(serve_pair(False),
+                                       borrowed=serve_pair(True),
+                                       workload="mixed 2D/3D uint8 / 14-bit uint16 requests in "
+                                                "pinned host memory, smoothed fields sigma=2 "
+                                                "(synth.request_mix); borrowed: "
+                                                "ecc_submit_borrowed")
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(img)
         print(json.dumps(line), flush=True)

@@ -216,6 +216,19 @@ int ecc_compute_batch(ecc_handle* h, int n, const ecc_image* images, ecc_result*
 int ecc_submit(ecc_handle* h, const void* image, const int64_t* dims, int ndim,
                ecc_dtype dtype, uint64_t* req_id);
 
+/* As ecc_submit, but an image in pinned host memory (cudaHostAlloc'd or
+ * registered) is borrowed instead of copied before the call returns: its
+ * device copy is enqueued on the server's copy stream (ordered before the
+ * request's batch) or, over the memory cap, made when the scheduler admits
+ * the request, and a streamed request reads its slabs from it. The caller
+ * keeps the buffer allocated and unchanged until ecc_poll has returned a
+ * status other than ECC_PENDING / ECC_ERR_TIMEOUT for the request (or the
+ * handle is destroyed). The call does not wait for the copy, so a submitting
+ * thread queues copies back to back. An image in pageable host memory is
+ * copied before the call returns, as by ecc_submit. Errors as ecc_submit. */
+int ecc_submit_borrowed(ecc_handle* h, const void* image, const int64_t* dims, int ndim,
+                        ecc_dtype dtype, uint64_t* req_id);
+
 /* Waits up to timeout_us microseconds (0 = just check) for request req_id.
  * ECC_OK: *out holds the curve and the request is retired. ECC_PENDING: not
  * done and timeout_us == 0. ECC_ERR_TIMEOUT: not done when the wait ran out.

@@ -629,6 +629,7 @@ struct Request {
   int64_t pitch = 0;      // row pitch of the device copy (bytes)
   size_t dev_bytes = 0;   // bytes of the device copy
   std::vector<unsigned char> host_copy;
+  const unsigned char* src = nullptr;  // host image: host_copy, or the caller's borrowed buffer
   void* d_img = nullptr;
   State state = kQueuedHost;
   int status = ECC_OK;
@@ -711,10 +712,10 @@ bool admit(ecc_handle* h, Server* sv, Request* r) {
   if (r->bytes) {
     const size_t dense = dtype_bytes(r->dtype) * (size_t)r->n[2];
     if ((size_t)r->pitch != dense)
-      e = cudaMemcpy2DAsync(d, (size_t)r->pitch, r->host_copy.data(), dense, dense,
+      e = cudaMemcpy2DAsync(d, (size_t)r->pitch, r->src, dense, dense,
                             (size_t)(r->n[0] * r->n[1]), cudaMemcpyHostToDevice, sv->copy_stream);
     else
-      e = cudaMemcpyAsync(d, r->host_copy.data(), r->bytes, cudaMemcpyHostToDevice,
+      e = cudaMemcpyAsync(d, r->src, r->bytes, cudaMemcpyHostToDevice,
                           sv->copy_stream);
     if (e) {
       cudaFreeAsync(d, sv->copy_stream);
@@ -726,6 +727,7 @@ bool admit(ecc_handle* h, Server* sv, Request* r) {
   r->d_img = d;
   r->host_copy.clear();
   r->host_copy.shrink_to_fit();
+  r->src = nullptr;
   r->state = Request::kOnDevice;
   sv->bytes_in_use += request_cost(r);
   return true;
@@ -867,6 +869,7 @@ bool job_step(ecc_handle* h, Server* sv, std::unique_lock<std::mutex>& lk) {
     r->t_done = std::chrono::steady_clock::now();
     r->host_copy.clear();
     r->host_copy.shrink_to_fit();
+    r->src = nullptr;
     sv->job = nullptr;
     job_release(sv, &j);
     return true;
@@ -884,7 +887,7 @@ bool job_step(ecc_handle* h, Server* sv, std::unique_lock<std::mutex>& lk) {
     }
     const int64_t cnz = std::min<int64_t>(r->depth, r->sn[0] - j.next_z);
     char* base = static_cast<char*>(j.ring) + (size_t)k * (r->depth + 2) * r->plane_bytes;
-    const unsigned char* src = r->host_copy.data() + (size_t)j.next_z * r->plane_bytes;
+    const unsigned char* src = r->src + (size_t)j.next_z * r->plane_bytes;
     lk.unlock();
     e = cudaMemcpyAsync(base + r->plane_bytes, src, (size_t)cnz * r->plane_bytes,
                         cudaMemcpyHostToDevice, sv->job_copy);
@@ -943,13 +946,16 @@ void serve_loop(ecc_handle* h) {
   const int nslots = (int)sv->eng.slots.size();
   while (true) {
     bool progressed = false;
-    // 1. retire finished batches
+    // 1. retire finished batches. The curves leave the slot's pinned arena
+    // without the lock: only this thread launches and retires slots, and no
+    // other thread touches a launched request before its state changes.
     for (int s = 0; s < nslots; ++s) {
-      auto& fl = sv->in_flight[s];
-      if (fl.empty()) continue;
+      if (sv->in_flight[s].empty()) continue;
       cudaError_t q = cudaEventQuery(sv->eng.slots[s].done);
       if (q == cudaErrorNotReady) continue;
-      const auto now = std::chrono::steady_clock::now();
+      std::vector<Request*> fl;
+      fl.swap(sv->in_flight[s]);
+      lk.unlock();
       for (size_t i = 0; i < fl.size(); ++i) {
         Request* r = fl[i];
         if (q != cudaSuccess) {
@@ -958,12 +964,15 @@ void serve_loop(ecc_handle* h) {
           r->status = slot_result(sv->eng.slots[s], sv->specs[s], (int)i, &r->result);
           r->result_bins = r->bins;
         }
+      }
+      if (q != cudaSuccess) cudaGetLastError();
+      const auto now = std::chrono::steady_clock::now();
+      lk.lock();
+      for (Request* r : fl) {
         r->state = r->status == ECC_OK ? Request::kDone : Request::kFailed;
         r->t_done = now;
         free_device_image(sv, r);
       }
-      if (q != cudaSuccess) cudaGetLastError();
-      fl.clear();
       progressed = true;
     }
     if (sv->stop) break;
@@ -1017,13 +1026,18 @@ void serve_loop(ecc_handle* h) {
         it = sv->queue.erase(it);
       }
       if (!batch.empty()) {
+        // the work list is built and launched without the lock (the batch's
+        // requests are launched: no other thread touches them)
         Slot& sl = sv->eng.slots[free_slot];
-        cudaEventRecord(sv->copy_ev, sv->copy_stream);  // all admitted copies
-        int rc = slot_run(h, sl, sv->eng.tune, specs, sv->copy_ev);
         for (Request* r : batch) {
           r->slot = free_slot;
           r->state = Request::kLaunched;
         }
+        sv->specs[free_slot] = std::move(specs);
+        lk.unlock();
+        cudaEventRecord(sv->copy_ev, sv->copy_stream);  // all admitted copies
+        const int rc = slot_run(h, sl, sv->eng.tune, sv->specs[free_slot], sv->copy_ev);
+        lk.lock();
         if (rc) {
           for (Request* r : batch) {
             r->state = Request::kFailed;
@@ -1032,8 +1046,7 @@ void serve_loop(ecc_handle* h) {
             free_device_image(sv, r);
           }
         } else {
-          sv->in_flight[free_slot] = batch;
-          sv->specs[free_slot] = specs;
+          sv->in_flight[free_slot] = std::move(batch);
         }
         progressed = true;
       }
@@ -1241,8 +1254,9 @@ int ecc_compute_batch(ecc_handle* h, int n, const ecc_image* images, ecc_result*
   }
 }
 
-int ecc_submit(ecc_handle* h, const void* image, const int64_t* dims, int ndim, ecc_dtype dtype,
-               uint64_t* req_id) {
+// ecc_submit (borrow = false) and ecc_submit_borrowed (borrow = true).
+static int submit_request(ecc_handle* h, const void* image, const int64_t* dims, int ndim,
+                          ecc_dtype dtype, uint64_t* req_id, bool borrow) {
   if (!h) return ECC_ERR_ARG;
   try {
     Shape s;
@@ -1281,10 +1295,11 @@ int ecc_submit(ecc_handle* h, const void* image, const int64_t* dims, int ndim, 
       delete r;
       return set_err(h, ECC_ERR_OOM, "request larger than the device memory cap");
     }
-    // The caller's buffer is copied before returning. Pinned host memory
-    // goes straight to the device if the cap allows (the call waits for that
-    // copy); otherwise the image is copied on the host and the scheduler
-    // moves it to the device when memory is available.
+    // Pinned host memory goes straight to the device if the cap allows;
+    // otherwise the scheduler moves the image to the device when memory is
+    // available, from a host copy or, when borrowing, from the caller's
+    // pinned buffer. Without borrowing the call waits for its copy; a
+    // borrowed request's copy is ordered before its batch on the copy stream.
     bool pinned = false;
     if (r->bytes) {
       cudaPointerAttributes at{};
@@ -1293,26 +1308,34 @@ int ecc_submit(ecc_handle* h, const void* image, const int64_t* dims, int ndim, 
       else
         cudaGetLastError();
     }
+    // the memory is reserved under the lock, the copy enqueued without it
     cudaEvent_t copied = nullptr;
-    {
+    bool reserved = false;
+    if (pinned && !r->streamed) {
       std::lock_guard<std::mutex> lk(sv->mu);
-      if (pinned && !r->streamed && sv->bytes_in_use + request_cost(r) <= h->cfg.mem_cap_bytes) {
-        void* d = nullptr;
-        cudaError_t e = cudaMallocAsync(&d, r->dev_bytes, sv->copy_stream);
-        if (e == cudaSuccess &&
-            (e = cudaMemcpyAsync(d, image, r->bytes, cudaMemcpyHostToDevice, sv->copy_stream)) ==
-                cudaSuccess &&
-            (e = cudaEventCreateWithFlags(&copied, cudaEventDisableTiming)) == cudaSuccess &&
-            (e = cudaEventRecord(copied, sv->copy_stream)) == cudaSuccess) {
-          r->d_img = d;
-          r->state = Request::kOnDevice;
-          sv->bytes_in_use += request_cost(r);
-        } else {
-          cudaGetLastError();
-          if (d) cudaFreeAsync(d, sv->copy_stream);
-          if (copied) cudaEventDestroy(copied);
-          copied = nullptr;
-        }
+      if (sv->bytes_in_use + request_cost(r) <= h->cfg.mem_cap_bytes) {
+        sv->bytes_in_use += request_cost(r);
+        reserved = true;
+      }
+    }
+    if (reserved) {
+      void* d = nullptr;
+      cudaError_t e = cudaMallocAsync(&d, r->dev_bytes, sv->copy_stream);
+      if (e == cudaSuccess &&
+          (e = cudaMemcpyAsync(d, image, r->bytes, cudaMemcpyHostToDevice, sv->copy_stream)) ==
+              cudaSuccess &&
+          (borrow ||
+           ((e = cudaEventCreateWithFlags(&copied, cudaEventDisableTiming)) == cudaSuccess &&
+            (e = cudaEventRecord(copied, sv->copy_stream)) == cudaSuccess))) {
+        r->d_img = d;
+        r->state = Request::kOnDevice;
+      } else {
+        cudaGetLastError();
+        if (d) cudaFreeAsync(d, sv->copy_stream);
+        if (copied) cudaEventDestroy(copied);
+        copied = nullptr;
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->bytes_in_use -= request_cost(r);
       }
     }
     if (copied) {
@@ -1324,9 +1347,14 @@ int ecc_submit(ecc_handle* h, const void* image, const int64_t* dims, int ndim, 
         delete r;
         return rc;
       }
-    } else {
-      r->host_copy.resize(r->bytes);
-      if (r->bytes) std::memcpy(r->host_copy.data(), image, r->bytes);
+    } else if (r->state != Request::kOnDevice) {
+      if (borrow && pinned) {
+        r->src = static_cast<const unsigned char*>(image);
+      } else {
+        r->host_copy.resize(r->bytes);
+        if (r->bytes) std::memcpy(r->host_copy.data(), image, r->bytes);
+        r->src = r->host_copy.data();
+      }
     }
     {
       std::lock_guard<std::mutex> lk(sv->mu);
@@ -1344,6 +1372,16 @@ int ecc_submit(ecc_handle* h, const void* image, const int64_t* dims, int ndim, 
   } catch (...) {
     return set_err(h, ECC_ERR_CUDA, "internal error");
   }
+}
+
+int ecc_submit(ecc_handle* h, const void* image, const int64_t* dims, int ndim, ecc_dtype dtype,
+               uint64_t* req_id) {
+  return submit_request(h, image, dims, ndim, dtype, req_id, false);
+}
+
+int ecc_submit_borrowed(ecc_handle* h, const void* image, const int64_t* dims, int ndim,
+                        ecc_dtype dtype, uint64_t* req_id) {
+  return submit_request(h, image, dims, ndim, dtype, req_id, true);
 }
 
 int ecc_poll(ecc_handle* h, uint64_t req_id, ecc_result* out, int64_t timeout_us) {

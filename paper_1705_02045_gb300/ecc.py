@@ -69,6 +69,7 @@ _SIGNATURES = {
                                   C.POINTER(ecc_result)]),
     "ecc_compute_batch": (C.c_int, [_P, C.c_int, C.POINTER(ecc_image), C.POINTER(ecc_result)]),
     "ecc_submit": (C.c_int, [_P, _P, _I64P, C.c_int, C.c_int, C.POINTER(C.c_uint64)]),
+    "ecc_submit_borrowed": (C.c_int, [_P, _P, _I64P, C.c_int, C.c_int, C.POINTER(C.c_uint64)]),
     "ecc_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(ecc_result), C.c_int64]),
     "ecc_request_latency_us": (C.c_int, [_P, C.c_uint64, C.POINTER(C.c_double)]),
     "ecc_launch_count": (C.c_int64, [_P]),
@@ -169,6 +170,8 @@ def ecc_create(config: ecc_config | None = None, **fields):
 
 def ecc_destroy(h) -> None:
     load().ecc_destroy(h)
+    for key in [k for k in _borrowed if k[0] == h.value]:
+        del _borrowed[key]
 
 
 def ecc_last_error(h) -> str:
@@ -304,11 +307,30 @@ def ecc_submit(h, image) -> int:
     return rid.value
 
 
+# images of borrowed requests, kept alive until their request has finished
+_borrowed = {}
+
+
+def ecc_submit_borrowed(h, image) -> int:
+    """ecc_submit without the copy on return: the library reads the image
+    (pinned host memory) until the request has finished; the binding holds a
+    reference to it until ecc_poll reports the request done or failed."""
+    lib = load()
+    ptr, keep = _data_ptr(image)
+    rid = C.c_uint64()
+    _check(h, lib.ecc_submit_borrowed(h, ptr, _dims(image.shape), len(image.shape),
+                                      _dtype_code(image.dtype), C.byref(rid)))
+    _borrowed[(h.value, rid.value)] = keep
+    return rid.value
+
+
 def ecc_poll(h, req_id: int, timeout_us: int = 0):
     """(status, curve or None)."""
     lib = load()
     r = ecc_result()
     rc = lib.ecc_poll(h, C.c_uint64(req_id), C.byref(r), int(timeout_us))
+    if rc not in (ECC_PENDING, ECC_ERR_TIMEOUT):
+        _borrowed.pop((h.value, req_id), None)
     if rc == ECC_OK:
         try:
             return rc, _result_to_numpy(r)

@@ -429,3 +429,56 @@ def test_serve_concurrent_submitters(lib):
     assert len(results) == len(imgs)
     for img, curve in results.values():
         assert np.array_equal(curve, oracle.ecc_int(img, 16384, "V"))
+
+
+def test_serve_borrowed_matches_oracle(lib):
+    """Borrowed submissions: pinned images are read in place (the call does not
+    wait for their copies), a pageable one in the same stream is copied; the
+    binding keeps a pinned image alive that the caller dropped at once."""
+    import torch
+    imgs = _mixed_images(40, S + 90, max2d=160, max3d=36)
+    pinned = [torch.from_numpy(img).pin_memory() for img, _ in imgs]
+    extra = synth.smooth_int((20, 30, 40), 1.0, 16383, S + 91, np.uint16)
+    h = ecc.ecc_create(device=0, bins=16384)
+    try:
+        ids = [ecc.ecc_submit_borrowed(h, t) for t in pinned]
+        ids.append(ecc.ecc_submit_borrowed(h, extra))  # pageable: copied
+        ids.append(ecc.ecc_submit_borrowed(h, torch.from_numpy(extra.copy()).pin_memory()))
+        got = []
+        for rid in ids:
+            st, curve = ecc.ecc_poll(h, rid, timeout_us=120_000_000)
+            assert st == ecc.ECC_OK
+            got.append(curve)
+        assert not [k for k in ecc._borrowed if k[0] == h.value]
+    finally:
+        ecc.ecc_destroy(h)
+    for (img, _), g in zip(imgs, got):
+        assert np.array_equal(g, oracle.ecc_int(img, 16384, "V"))
+    want = oracle.ecc_int(extra, 16384, "V")
+    assert np.array_equal(got[-2], want) and np.array_equal(got[-1], want)
+
+
+def test_serve_borrowed_over_cap_and_streamed(lib):
+    """Borrowed pinned images under a cap of three requests (admitted later,
+    copied from the caller's buffer) and two requests larger than the ring
+    (slabs read from the caller's buffer), against the oracle."""
+    import torch
+    small = [synth.smooth_u8((24, 64, 64), 2.0, S + 95 + i) for i in range(9)]
+    big3 = synth.two_phase_u16((60, 40, 130), 1.5, S + 96)
+    big2 = synth.smooth_int((700, 500), 2.0, 16383, S + 97, np.uint16)
+    order = [big3] + small[:5] + [big2] + small[5:]
+    one = 24 * 64 * 64 + 8 * (2 * 16384 + 1)
+    h = ecc.ecc_create(device=0, bins=16384, ring_bytes=256 * 1024, slab_depth=8,
+                       mem_cap_bytes=3 * one)
+    try:
+        bufs = [torch.from_numpy(img).pin_memory() for img in order]
+        ids = [ecc.ecc_submit_borrowed(h, t) for t in bufs]
+        got = []
+        for rid in ids:
+            st, curve = ecc.ecc_poll(h, rid, timeout_us=120_000_000)
+            assert st == ecc.ECC_OK
+            got.append(curve)
+    finally:
+        ecc.ecc_destroy(h)
+    for img, g in zip(order, got):
+        assert np.array_equal(g, oracle.ecc_int(img, 16384, "V"))

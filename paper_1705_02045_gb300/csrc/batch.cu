@@ -270,6 +270,7 @@ struct Slot {
   DevBuf arena;
   unsigned char* h_arena = nullptr;
   size_t h_arena_cap = 0;
+  std::vector<unsigned char*> h_retired;  // outgrown pinned arenas, freed with the slot
   DevBuf staging;  // device copies of the batch's host images (dense rows)
   cudaGraphExec_t exec_small = nullptr, exec_large = nullptr;
   cudaEvent_t done = nullptr;
@@ -394,6 +395,7 @@ void slot_free(Slot& sl) {
   if (sl.exec_large) cudaGraphExecDestroy(sl.exec_large);
   if (sl.h_desc) cudaFreeHost(sl.h_desc);
   if (sl.h_arena) cudaFreeHost(sl.h_arena);
+  for (unsigned char* p : sl.h_retired) cudaFreeHost(p);
   sl.desc.release();
   sl.arena.release();
   sl.staging.release();
@@ -476,8 +478,11 @@ int tune_depth(BatchTune& t, Slot& sl) {
   return BatchTune::kDepth[sl.tune_cand];
 }
 
+// h_res: pinned destination of the (curve, error word) records, at the
+// offsets sl.res_off (results_bytes(specs) bytes); null = the slot's own
+// pinned arena.
 int slot_run(ecc_handle* h, Slot& sl, BatchTune& tune, const std::vector<ImgSpec>& specs,
-             cudaEvent_t wait_ev) {
+             cudaEvent_t wait_ev, unsigned char* h_res = nullptr) {
   cudaError_t e;
   const int n = (int)specs.size();
   const int depth = tune_depth(tune, sl);
@@ -494,16 +499,26 @@ int slot_run(ecc_handle* h, Slot& sl, BatchTune& tune, const std::vector<ImgSpec
     sl.res_off[i] = res_total;
     res_total += sizeof(long long) * (sp.bins + 1);
   }
+  // Arenas grow geometrically and without waiting for the device: the device
+  // one in stream order on the slot's stream (a plain free would wait for
+  // every copy and batch in flight), the pinned one keeping its outgrown
+  // buffers until the slot is freed.
   const size_t arena_total = vcec_total + res_total;
-  if ((e = sl.arena.ensure(arena_total))) return cuda_err(h, e, "batch arena");
-  if (sl.h_arena_cap < res_total) {
-    if (sl.h_arena) cudaFreeHost(sl.h_arena);
-    sl.h_arena = nullptr;
-    if ((e = cudaMallocHost(&sl.h_arena, res_total))) {
-      sl.h_arena_cap = 0;
-      return cuda_err(h, e, "pinned arena");
-    }
-    sl.h_arena_cap = res_total;
+  if (arena_total > sl.arena.cap || !sl.arena.p) {
+    const size_t want = std::max(arena_total, 2 * sl.arena.cap);
+    if (sl.arena.p) cudaFreeAsync(sl.arena.p, sl.stream);
+    sl.arena.p = nullptr;
+    sl.arena.cap = 0;
+    if ((e = cudaMallocAsync(&sl.arena.p, want, sl.stream))) return cuda_err(h, e, "batch arena");
+    sl.arena.cap = want;
+  }
+  if (!h_res && sl.h_arena_cap < res_total) {
+    const size_t want = std::max(res_total, 2 * sl.h_arena_cap);
+    unsigned char* p = nullptr;
+    if ((e = cudaMallocHost(&p, want))) return cuda_err(h, e, "pinned arena");
+    if (sl.h_arena) sl.h_retired.push_back(sl.h_arena);
+    sl.h_arena = p;
+    sl.h_arena_cap = want;
   }
   BHeader* hdr = reinterpret_cast<BHeader*>(sl.h_desc + sl.L.hdr);
   BImage* imgs = reinterpret_cast<BImage*>(sl.h_desc + sl.L.imgs);
@@ -581,10 +596,25 @@ int slot_run(ecc_handle* h, Slot& sl, BatchTune& tune, const std::vector<ImgSpec
     if (bits_vox > 0) sl.tune_vox = bits_vox;
     else sl.tune_cand = -1;  // nothing to learn from a batch without bit-sliced images
   }
-  if ((e = cudaMemcpyAsync(sl.h_arena, abase + vcec_total, res_total, cudaMemcpyDeviceToHost,
-                           sl.stream)) ||
+  if ((e = cudaMemcpyAsync(h_res ? h_res : sl.h_arena, abase + vcec_total, res_total,
+                           cudaMemcpyDeviceToHost, sl.stream)) ||
       (e = cudaEventRecord(sl.done, sl.stream)))
     return cuda_err(h, e, "copy results");
+  return ECC_OK;
+}
+
+// Bytes of the (curve, error word) records of a batch.
+size_t results_bytes(const std::vector<ImgSpec>& specs) {
+  size_t t = 0;
+  for (const ImgSpec& sp : specs) t += sizeof(long long) * (sp.bins + 1);
+  return t;
+}
+
+// Status of a (curve, error word) record from its error word.
+int record_status(const long long* rec, int64_t bins) {
+  const int err = *reinterpret_cast<const int*>(rec + bins);
+  if (err & kErrValue) return ECC_ERR_VALUE;
+  if (err & kErrOverflow) return ECC_ERR_CUDA;
   return ECC_OK;
 }
 
@@ -592,9 +622,8 @@ int slot_run(ecc_handle* h, Slot& sl, BatchTune& tune, const std::vector<ImgSpec
 int slot_result(const Slot& sl, const std::vector<ImgSpec>& specs, int i, int64_t** curve) {
   const long long* rec = reinterpret_cast<const long long*>(sl.h_arena + sl.res_off[i]);
   const int64_t bins = specs[i].bins;
-  const int err = *reinterpret_cast<const int*>(rec + bins);
-  if (err & kErrValue) return ECC_ERR_VALUE;
-  if (err & kErrOverflow) return ECC_ERR_CUDA;
+  const int st = record_status(rec, bins);
+  if (st != ECC_OK) return st;
   *curve = static_cast<int64_t*>(std::malloc(sizeof(int64_t) * std::max<int64_t>(bins, 1)));
   if (!*curve) return ECC_ERR_OOM;
   std::memcpy(*curve, rec, sizeof(int64_t) * bins);
@@ -619,6 +648,19 @@ int64_t staged_pitch(const ecc_handle*, int dtype, int64_t, int64_t nx) {
 // Serving
 // ---------------------------------------------------------------------------
 
+// Pinned host memory that receives served batches' (curve, error word)
+// records: each batch takes one contiguous range, bump-allocated. live counts
+// the batches in flight plus the polled-for records in it (under the server
+// lock); a slab with nothing live starts over. So the request loop only reads
+// error words, and ecc_poll copies a curve out.
+struct PinnedSlab {
+  unsigned char* p = nullptr;
+  size_t cap = 0;
+  size_t used = 0;
+  int live = 0;
+};
+constexpr size_t kSlabBytes = size_t(64) << 20;
+
 struct Request {
   enum State { kQueuedHost, kOnDevice, kLaunched, kStreaming, kDone, kFailed, kRetired };
   uint64_t id = 0;
@@ -631,10 +673,13 @@ struct Request {
   std::vector<unsigned char> host_copy;
   const unsigned char* src = nullptr;  // host image: host_copy, or the caller's borrowed buffer
   void* d_img = nullptr;
+  cudaEvent_t copy_done = nullptr;  // device copy still in flight on the copy stream, else null
   State state = kQueuedHost;
   int status = ECC_OK;
   int64_t* result = nullptr;
   int64_t result_bins = 0;
+  PinnedSlab* slab = nullptr;  // or: the curve sits in this slab at slab_off
+  size_t slab_off = 0;
   std::chrono::steady_clock::time_point t_submit, t_done;
   int slot = -1;
   // streamed requests (device copy larger than the ring): z-slab plan
@@ -670,13 +715,22 @@ struct Server {
   std::mutex mu;
   std::condition_variable cv;
   std::thread th;
+  // completion thread: copies finished batches' curves out of their slabs
+  std::thread done_th;
+  std::condition_variable done_cv;
+  std::deque<std::pair<std::vector<Request*>, PinnedSlab*>> done_q;
   bool stop = false;
   uint64_t next_id = 1;
   std::deque<Request*> queue;  // waiting for a launch, FIFO
   std::map<uint64_t, Request*> all;
   int64_t bytes_in_use = 0;
   cudaStream_t copy_stream = nullptr;
-  cudaEvent_t copy_ev = nullptr;
+  std::vector<cudaEvent_t> ev_pool;  // copy-completion events for reuse
+  int pending_copies = 0;            // requests with copy_done set
+  std::deque<Request*> copying;      // requests whose copies were enqueued, in that order
+  std::vector<PinnedSlab*> slabs;   // result slabs (freed at shutdown)
+  PinnedSlab* cur_slab = nullptr;   // the slab batches allocate from
+  std::vector<std::pair<PinnedSlab*, size_t>> slot_res;  // per slot: its batch's records
   BatchEngine eng;
   std::vector<std::vector<Request*>> in_flight;  // per slot
   std::vector<std::vector<ImgSpec>> specs;       // per slot
@@ -700,9 +754,115 @@ void free_device_image(Server* sv, Request* r) {
   }
 }
 
-// Moves a host-staged request to the device if it fits (caller holds mu).
+// Copy-completion events from the pool (caller holds mu); null if none can
+// be made.
+cudaEvent_t take_event(Server* sv) {
+  if (!sv->ev_pool.empty()) {
+    cudaEvent_t e = sv->ev_pool.back();
+    sv->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Marks r's device copy as in flight behind event e (caller holds mu).
+void track_copy(Server* sv, Request* r, cudaEvent_t e) {
+  r->copy_done = e;
+  ++sv->pending_copies;
+  sv->copying.push_back(r);
+}
+
+// Whether r's device copy has finished; returns its event to the pool when it
+// has (caller holds mu). A failed copy counts as finished: the batch launch
+// then reports the error.
+bool copy_finished(Server* sv, Request* r) {
+  if (!r->copy_done) return true;
+  const cudaError_t q = cudaEventQuery(r->copy_done);
+  if (q == cudaErrorNotReady) return false;
+  if (q != cudaSuccess) cudaGetLastError();
+  sv->ev_pool.push_back(r->copy_done);
+  r->copy_done = nullptr;
+  --sv->pending_copies;
+  return true;
+}
+
+// Retires the finished copies at the front of the copy order (caller holds
+// mu), so that admission can enqueue more while both slots compute.
+void reap_copies(Server* sv) {
+  while (!sv->copying.empty()) {
+    Request* r = sv->copying.front();
+    if (r->copy_done && !copy_finished(sv, r)) break;
+    sv->copying.pop_front();
+  }
+}
+
+// A range of `need` bytes for one batch's records (caller holds mu): from the
+// current slab, else from a slab with nothing live, else null (the caller
+// adds a slab). The batch holds one live count until it is retired.
+PinnedSlab* take_records(Server* sv, size_t need, size_t* off) {
+  need = (need + 255) & ~size_t(255);
+  auto try_slab = [&](PinnedSlab* sb) {
+    if (sb->live == 0) sb->used = 0;
+    if (sb->cap - sb->used < need) return false;
+    *off = sb->used;
+    sb->used += need;
+    ++sb->live;
+    sv->cur_slab = sb;
+    return true;
+  };
+  if (sv->cur_slab && try_slab(sv->cur_slab)) return sv->cur_slab;
+  for (PinnedSlab* sb : sv->slabs)
+    if (sb != sv->cur_slab && try_slab(sb)) return sb;
+  return nullptr;
+}
+
+// Whether the next batch goes now (caller holds mu): at once when no batch
+// is in flight, else once it holds kFillRequests requests or kFillVoxels
+// voxels or its oldest request has waited kFillWaitUs, so that a stream of
+// requests under load fills batches instead of launching one graph (about
+// 50 us of fixed GPU time) per request or two.
+constexpr int kFillRequests = 32;
+constexpr double kFillVoxels = 64e6;
+constexpr int64_t kFillWaitUs = 200;
+bool batch_worth_launching(Server* sv) {
+  bool busy = false;
+  for (const auto& fl : sv->in_flight) busy = busy || !fl.empty();
+  if (!busy) return true;
+  int ready = 0;
+  double vox = 0;
+  bool in_flight_seen = false;
+  auto oldest = std::chrono::steady_clock::time_point::max();
+  for (Request* r : sv->queue) {
+    if (r->state != Request::kOnDevice) continue;
+    if (r->copy_done && (in_flight_seen || !copy_finished(sv, r))) {
+      in_flight_seen = true;
+      continue;
+    }
+    ++ready;
+    vox += (double)r->n[0] * (double)r->n[1] * (double)r->n[2];
+    oldest = std::min(oldest, r->t_submit);
+    if (ready >= kFillRequests || vox >= kFillVoxels) return true;
+  }
+  return ready > 0 && std::chrono::steady_clock::now() - oldest >=
+                          std::chrono::microseconds(kFillWaitUs);
+}
+
+// Copies queued on the copy stream at a time by admission: enough to keep
+// the copy engine busy between two passes of the request loop, few enough
+// that enqueueing never waits for room in the stream (a thread blocked there
+// holds up every other thread's CUDA calls).
+constexpr int kMaxPendingCopies = 64;
+
+// Moves a host-staged request to the device if it fits under the memory cap
+// and the copy limit (caller holds mu).
 bool admit(ecc_handle* h, Server* sv, Request* r) {
   if (sv->bytes_in_use + request_cost(r) > h->cfg.mem_cap_bytes) return false;
+  if (sv->pending_copies >= kMaxPendingCopies) return false;
   void* d = nullptr;
   cudaError_t e = cudaMallocAsync(&d, std::max<size_t>(r->dev_bytes, 1), sv->copy_stream);
   if (e) {
@@ -722,6 +882,17 @@ bool admit(ecc_handle* h, Server* sv, Request* r) {
       r->state = Request::kFailed;
       r->status = ECC_ERR_CUDA;
       return true;
+    }
+  }
+  if (r->bytes) {
+    cudaEvent_t ev = take_event(sv);
+    if (ev && cudaEventRecord(ev, sv->copy_stream) == cudaSuccess) {
+      track_copy(sv, r, ev);
+    } else {
+      // untracked: wait for the copy here (rare)
+      cudaGetLastError();
+      if (ev) sv->ev_pool.push_back(ev);
+      cudaStreamSynchronize(sv->copy_stream);
     }
   }
   r->d_img = d;
@@ -939,6 +1110,36 @@ bool job_step(ecc_handle* h, Server* sv, std::unique_lock<std::mutex>& lk) {
   return progressed;
 }
 
+// Completion thread: each retired batch's curves out of its pinned slab into
+// the requests' own buffers, then the requests are done (ecc_poll returns
+// them) and their slab range is released. Runs beside the request loop, so
+// copying results does not hold up admissions and launches.
+void done_loop(Server* sv) {
+  std::unique_lock<std::mutex> lk(sv->mu);
+  while (true) {
+    sv->done_cv.wait(lk, [&] { return sv->stop || !sv->done_q.empty(); });
+    if (sv->stop) break;
+    auto item = std::move(sv->done_q.front());
+    sv->done_q.pop_front();
+    lk.unlock();
+    for (Request* r : item.first) {
+      const int64_t bins = r->result_bins;
+      r->result = static_cast<int64_t*>(std::malloc(sizeof(int64_t) * std::max<int64_t>(bins, 1)));
+      if (r->result) std::memcpy(r->result, r->slab->p + r->slab_off, sizeof(int64_t) * bins);
+      else r->status = ECC_ERR_OOM;
+    }
+    const auto now = std::chrono::steady_clock::now();
+    lk.lock();
+    for (Request* r : item.first) {
+      r->slab = nullptr;
+      r->state = r->status == ECC_OK ? Request::kDone : Request::kFailed;
+      r->t_done = now;
+    }
+    item.second->live -= (int)item.first.size();
+    sv->cv.notify_all();
+  }
+}
+
 void serve_loop(ecc_handle* h) {
   Server* sv = h->server;
   cudaSetDevice(h->device);
@@ -946,7 +1147,8 @@ void serve_loop(ecc_handle* h) {
   const int nslots = (int)sv->eng.slots.size();
   while (true) {
     bool progressed = false;
-    // 1. retire finished batches. The curves leave the slot's pinned arena
+    // 1. retire finished batches: statuses from the error words in the
+    // batch's pinned records (the curves stay there until polled), read
     // without the lock: only this thread launches and retires slots, and no
     // other thread touches a launched request before its state changes.
     for (int s = 0; s < nslots; ++s) {
@@ -955,29 +1157,61 @@ void serve_loop(ecc_handle* h) {
       if (q == cudaErrorNotReady) continue;
       std::vector<Request*> fl;
       fl.swap(sv->in_flight[s]);
+      PinnedSlab* sb = sv->slot_res[s].first;
+      const size_t base = sv->slot_res[s].second;
+      sv->slot_res[s] = {nullptr, 0};
       lk.unlock();
+      int held = 0;  // records that stay in the slab until polled
       for (size_t i = 0; i < fl.size(); ++i) {
         Request* r = fl[i];
         if (q != cudaSuccess) {
           r->status = ECC_ERR_CUDA;
-        } else {
-          r->status = slot_result(sv->eng.slots[s], sv->specs[s], (int)i, &r->result);
+          continue;
+        }
+        const size_t off = base + sv->eng.slots[s].res_off[i];
+        r->status = record_status(reinterpret_cast<const long long*>(sb->p + off), r->bins);
+        if (r->status == ECC_OK) {
+          r->slab = sb;
+          r->slab_off = off;
           r->result_bins = r->bins;
+          ++held;
         }
       }
       if (q != cudaSuccess) cudaGetLastError();
       const auto now = std::chrono::steady_clock::now();
+      // images freed on the slot's stream (idle: its batch is done), not on
+      // the copy stream, where a free would queue behind pending copies
+      for (Request* r : fl)
+        if (r->d_img) cudaFreeAsync(r->d_img, sv->eng.slots[s].stream);
       lk.lock();
+      // failed requests finish here; the others when the completion thread
+      // has copied their curves (the slab range is held until then)
+      sb->live += held - 1;
+      std::vector<Request*> ok;
+      ok.reserve(held);
       for (Request* r : fl) {
-        r->state = r->status == ECC_OK ? Request::kDone : Request::kFailed;
-        r->t_done = now;
-        free_device_image(sv, r);
+        if (r->d_img) {
+          r->d_img = nullptr;
+          sv->bytes_in_use -= request_cost(r);
+        }
+        if (r->status == ECC_OK) {
+          ok.push_back(r);
+        } else {
+          r->state = Request::kFailed;
+          r->t_done = now;
+        }
+      }
+      if (!ok.empty()) {
+        sv->done_q.emplace_back(std::move(ok), sb);
+        sv->done_cv.notify_one();
       }
       progressed = true;
     }
     if (sv->stop) break;
-    // 2. admit host-staged requests in arrival order while memory allows; a
-    // streamed request starts when no other one streams and its ring fits
+    // 2. admit host-staged requests in arrival order while memory and the
+    // copy limit allow; a streamed request starts when no other one streams
+    // and its ring fits
+    reap_copies(sv);
     for (auto it = sv->queue.begin(); it != sv->queue.end();) {
       Request* r = *it;
       if (r->state != Request::kQueuedHost) {
@@ -1007,19 +1241,30 @@ void serve_loop(ecc_handle* h) {
         free_slot = s;
         break;
       }
+    if (free_slot >= 0 && !batch_worth_launching(sv)) free_slot = -1;
     if (free_slot >= 0) {
+      // requests whose device copy has finished; copies finish in the order
+      // they were enqueued, so after the first one still in flight the later
+      // ones are not queried (they wait for the next round)
       std::vector<Request*> batch;
       std::vector<ImgSpec> specs;
+      bool in_flight_seen = false;
+      size_t rec_bytes = 0;  // the batch's result records fit one slab
       for (auto it = sv->queue.begin(); it != sv->queue.end() && (int)batch.size() < kMaxBatch;) {
         Request* r = *it;
         if (r->state == Request::kFailed) {
           it = sv->queue.erase(it);
           continue;
         }
-        if (r->state != Request::kOnDevice) {
+        if (r->state != Request::kOnDevice ||
+            (r->copy_done && (in_flight_seen || !copy_finished(sv, r)))) {
+          in_flight_seen = in_flight_seen || r->copy_done != nullptr;
           ++it;
           continue;
         }
+        const size_t rb = sizeof(long long) * (r->bins + 1);
+        if (!batch.empty() && rec_bytes + rb > kSlabBytes) break;
+        rec_bytes += rb;
         batch.push_back(r);
         specs.push_back(
             ImgSpec{r->d_img, {r->n[0], r->n[1], r->n[2]}, r->dtype, r->bins, r->pitch});
@@ -1034,11 +1279,33 @@ void serve_loop(ecc_handle* h) {
           r->state = Request::kLaunched;
         }
         sv->specs[free_slot] = std::move(specs);
+        // the batch's records: a range of a pinned slab (a new slab, if
+        // none has room, is allocated without the lock)
+        const size_t need = results_bytes(sv->specs[free_slot]);
+        size_t off = 0;
+        PinnedSlab* sb = take_records(sv, need, &off);
         lk.unlock();
-        cudaEventRecord(sv->copy_ev, sv->copy_stream);  // all admitted copies
-        const int rc = slot_run(h, sl, sv->eng.tune, sv->specs[free_slot], sv->copy_ev);
+        int rc = ECC_OK;
+        PinnedSlab* fresh = nullptr;
+        if (!sb) {
+          fresh = new PinnedSlab();
+          fresh->cap = std::max(kSlabBytes, (need + 255) & ~size_t(255));
+          if (cudaMallocHost(&fresh->p, fresh->cap) != cudaSuccess) {
+            cudaGetLastError();
+            delete fresh;
+            fresh = nullptr;
+            rc = set_err(h, ECC_ERR_OOM, "pinned result slab");
+          }
+        }
+        if (fresh) {
+          std::lock_guard<std::mutex> lk2(sv->mu);
+          sv->slabs.push_back(fresh);
+          sb = take_records(sv, need, &off);  // fits: the new slab is empty
+        }
+        if (!rc) rc = slot_run(h, sl, sv->eng.tune, sv->specs[free_slot], nullptr, sb->p + off);
         lk.lock();
         if (rc) {
+          if (sb) --sb->live;
           for (Request* r : batch) {
             r->state = Request::kFailed;
             r->status = rc;
@@ -1047,6 +1314,7 @@ void serve_loop(ecc_handle* h) {
           }
         } else {
           sv->in_flight[free_slot] = std::move(batch);
+          sv->slot_res[free_slot] = {sb, off};
         }
         progressed = true;
       }
@@ -1055,7 +1323,7 @@ void serve_loop(ecc_handle* h) {
       sv->cv.notify_all();
       continue;
     }
-    bool busy = sv->job != nullptr;
+    bool busy = sv->job != nullptr || sv->pending_copies > 0;
     for (int s = 0; s < nslots; ++s) busy = busy || !sv->in_flight[s].empty();
     if (busy) {
       // work on the GPU: poll for a finished batch or a new request without
@@ -1086,8 +1354,7 @@ int server_start(ecc_handle* h) {
   cudaError_t e;
   if ((e = cudaStreamCreateWithFlags(&sv->copy_stream, cudaStreamNonBlocking)) ||
       (e = cudaStreamCreateWithFlags(&sv->job_stream, cudaStreamNonBlocking)) ||
-      (e = cudaStreamCreateWithFlags(&sv->job_copy, cudaStreamNonBlocking)) ||
-      (e = cudaEventCreateWithFlags(&sv->copy_ev, cudaEventDisableTiming))) {
+      (e = cudaStreamCreateWithFlags(&sv->job_copy, cudaStreamNonBlocking))) {
     delete sv;
     return cuda_err(h, e, "server streams");
   }
@@ -1102,6 +1369,7 @@ int server_start(ecc_handle* h) {
   }
   sv->in_flight.resize(2);
   sv->specs.resize(2);
+  sv->slot_res.assign(2, {nullptr, 0});
   // keep freed stream-ordered allocations cached in the pool
   cudaMemPool_t pool;
   if (cudaDeviceGetDefaultMemPool(&pool, h->device) == cudaSuccess) {
@@ -1110,6 +1378,7 @@ int server_start(ecc_handle* h) {
   }
   h->server = sv;
   sv->th = std::thread(serve_loop, h);
+  sv->done_th = std::thread(done_loop, sv);
   return ECC_OK;
 }
 
@@ -1123,7 +1392,9 @@ void serve_shutdown(ecc_handle* h) {
       sv->stop = true;
     }
     sv->cv.notify_all();
+    sv->done_cv.notify_all();
     if (sv->th.joinable()) sv->th.join();
+    if (sv->done_th.joinable()) sv->done_th.join();
     cudaSetDevice(h->device);
     for (Slot& sl : sv->eng.slots) slot_free(sl);
     if (sv->job) job_release(sv, sv->job);
@@ -1131,11 +1402,16 @@ void serve_shutdown(ecc_handle* h) {
     for (auto& kv : sv->all) {
       Request* r = kv.second;
       if (r->d_img) cudaFreeAsync(r->d_img, sv->copy_stream);
+      if (r->copy_done) cudaEventDestroy(r->copy_done);
       std::free(r->result);
       delete r;
     }
     cudaStreamSynchronize(sv->copy_stream);
-    cudaEventDestroy(sv->copy_ev);
+    for (cudaEvent_t e : sv->ev_pool) cudaEventDestroy(e);
+    for (PinnedSlab* sb : sv->slabs) {
+      cudaFreeHost(sb->p);
+      delete sb;
+    }
     cudaStreamDestroy(sv->copy_stream);
     cudaStreamDestroy(sv->job_stream);
     cudaStreamDestroy(sv->job_copy);
@@ -1295,11 +1571,12 @@ static int submit_request(ecc_handle* h, const void* image, const int64_t* dims,
       delete r;
       return set_err(h, ECC_ERR_OOM, "request larger than the device memory cap");
     }
-    // Pinned host memory goes straight to the device if the cap allows;
-    // otherwise the scheduler moves the image to the device when memory is
-    // available, from a host copy or, when borrowing, from the caller's
-    // pinned buffer. Without borrowing the call waits for its copy; a
-    // borrowed request's copy is ordered before its batch on the copy stream.
+    // Without borrowing, pinned host memory goes straight to the device if
+    // the cap allows and the call waits for that copy; otherwise the image
+    // is copied on the host. A borrowed pinned image is read in place: it is
+    // admitted like a host copy (by the scheduler, or here if there is room),
+    // its copy enqueued under the limit on copies in flight, and the request
+    // joins a batch once that copy's event has completed.
     bool pinned = false;
     if (r->bytes) {
       cudaPointerAttributes at{};
@@ -1308,14 +1585,38 @@ static int submit_request(ecc_handle* h, const void* image, const int64_t* dims,
       else
         cudaGetLastError();
     }
-    // the memory is reserved under the lock, the copy enqueued without it
-    cudaEvent_t copied = nullptr;
+    // The memory (and, when borrowing, a place in the window of copies in
+    // flight) is reserved under the lock, the copy enqueued without it. A
+    // borrowing caller whose window is full waits for the oldest copy in
+    // flight, without the lock.
+    cudaEvent_t copied = nullptr;  // the copy's completion event
     bool reserved = false;
     if (pinned && !r->streamed) {
-      std::lock_guard<std::mutex> lk(sv->mu);
-      if (sv->bytes_in_use + request_cost(r) <= h->cfg.mem_cap_bytes) {
+      const auto deadline = std::chrono::steady_clock::now() + std::chrono::seconds(300);
+      std::unique_lock<std::mutex> lk(sv->mu);
+      while (sv->bytes_in_use + request_cost(r) <= h->cfg.mem_cap_bytes) {
+        if (borrow) {
+          reap_copies(sv);
+          if (sv->pending_copies >= kMaxPendingCopies) {
+            cudaEvent_t oldest = sv->copying.empty() ? nullptr : sv->copying.front()->copy_done;
+            lk.unlock();
+            // (the event may be recycled meanwhile: then this waits for a
+            // later copy, which ends too)
+            while (oldest && cudaEventQuery(oldest) == cudaErrorNotReady &&
+                   std::chrono::steady_clock::now() < deadline)
+              std::this_thread::yield();
+            if (!oldest) std::this_thread::yield();
+            cudaGetLastError();
+            lk.lock();
+            if (std::chrono::steady_clock::now() >= deadline) break;  // left to admission
+            continue;
+          }
+        }
+        if ((copied = take_event(sv)) == nullptr) break;
         sv->bytes_in_use += request_cost(r);
+        if (borrow) ++sv->pending_copies;
         reserved = true;
+        break;
       }
     }
     if (reserved) {
@@ -1324,25 +1625,29 @@ static int submit_request(ecc_handle* h, const void* image, const int64_t* dims,
       if (e == cudaSuccess &&
           (e = cudaMemcpyAsync(d, image, r->bytes, cudaMemcpyHostToDevice, sv->copy_stream)) ==
               cudaSuccess &&
-          (borrow ||
-           ((e = cudaEventCreateWithFlags(&copied, cudaEventDisableTiming)) == cudaSuccess &&
-            (e = cudaEventRecord(copied, sv->copy_stream)) == cudaSuccess))) {
+          (e = cudaEventRecord(copied, sv->copy_stream)) == cudaSuccess) {
         r->d_img = d;
         r->state = Request::kOnDevice;
       } else {
         cudaGetLastError();
         if (d) cudaFreeAsync(d, sv->copy_stream);
-        if (copied) cudaEventDestroy(copied);
-        copied = nullptr;
         std::lock_guard<std::mutex> lk(sv->mu);
+        sv->ev_pool.push_back(copied);
+        copied = nullptr;
         sv->bytes_in_use -= request_cost(r);
+        if (borrow) --sv->pending_copies;
       }
+    }
+    if (copied && borrow) {
+      // tracked by the request loop (counted in pending_copies above)
+      r->copy_done = copied;
+      copied = nullptr;
     }
     if (copied) {
       const int rc = wait_event(h, copied, 300LL * 1000 * 1000);
-      cudaEventDestroy(copied);
+      std::lock_guard<std::mutex> lk(sv->mu);
+      sv->ev_pool.push_back(copied);
       if (rc) {
-        std::lock_guard<std::mutex> lk(sv->mu);
         free_device_image(sv, r);
         delete r;
         return rc;
@@ -1360,6 +1665,7 @@ static int submit_request(ecc_handle* h, const void* image, const int64_t* dims,
       std::lock_guard<std::mutex> lk(sv->mu);
       r->id = sv->next_id++;
       sv->all[r->id] = r;
+      if (r->copy_done) sv->copying.push_back(r);
       if (r->state == Request::kQueuedHost && !r->streamed) admit(h, sv, r);
       sv->queue.push_back(r);
       *req_id = r->id;
@@ -1401,13 +1707,13 @@ int ecc_poll(ecc_handle* h, uint64_t req_id, ecc_result* out, int64_t timeout_us
   std::memset(out, 0, sizeof *out);
   out->status = r->status;
   const int rc = r->status;
+  r->state = Request::kRetired;
   if (rc == ECC_OK) {
     out->owned = 1;
     out->bins = r->result_bins;
     out->curve = r->result;
     r->result = nullptr;
   }
-  r->state = Request::kRetired;
   return rc;
 }
 

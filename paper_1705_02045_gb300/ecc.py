@@ -139,14 +139,44 @@ def _data_ptr(image):
     return C.c_void_p(image.data_ptr()), image
 
 
+class _ResultOwner:
+    """Holds a library-allocated ecc_result whose buffers numpy arrays view;
+    releases them (ecc_result_free) when the last view is gone."""
+    __slots__ = ("r",)
+
+    def __init__(self, r: ecc_result):
+        self.r = ecc_result()
+        C.memmove(C.byref(self.r), C.byref(r), C.sizeof(ecc_result))
+
+    def __del__(self):
+        if _lib is not None:
+            _lib.ecc_result_free(C.byref(self.r))
+
+
+def _view(owner, ptr, n: int, ctype, dtype):
+    buf = (ctype * n).from_address(C.cast(ptr, C.c_void_p).value)
+    buf._owner = owner  # the buffer lives while any array viewing it does
+    return np.frombuffer(buf, dtype=dtype)
+
+
 def _result_to_numpy(r: ecc_result):
-    if r.bins > 0:
-        return np.ctypeslib.as_array(r.curve, shape=(r.bins,)).copy()
-    if r.npairs > 0:
-        t = np.ctypeslib.as_array(r.thresholds, shape=(r.npairs,)).copy()
-        chi = np.ctypeslib.as_array(r.chi, shape=(r.npairs,)).copy()
-        return t, chi
-    return np.zeros(0, np.float32), np.zeros(0, np.int64)
+    """The curve (or (thresholds, chi) pairs) of r as numpy arrays. Buffers
+    the library allocated are viewed in place and taken over (r is left
+    empty, so a later ecc_result_free of it is a no-op); others are copied."""
+    bins, npairs = int(r.bins), int(r.npairs)
+    if not r.owned or (bins <= 0 and npairs <= 0):
+        if bins > 0:
+            return np.ctypeslib.as_array(r.curve, shape=(bins,)).copy()
+        if npairs > 0:
+            return (np.ctypeslib.as_array(r.thresholds, shape=(npairs,)).copy(),
+                    np.ctypeslib.as_array(r.chi, shape=(npairs,)).copy())
+        return np.zeros(0, np.float32), np.zeros(0, np.int64)
+    owner = _ResultOwner(r)
+    C.memset(C.byref(r), 0, C.sizeof(ecc_result))
+    if bins > 0:
+        return _view(owner, owner.r.curve, bins, C.c_int64, np.int64)
+    return (_view(owner, owner.r.thresholds, npairs, C.c_float, np.float32),
+            _view(owner, owner.r.chi, npairs, C.c_int64, np.int64))
 
 
 def ecc_config_default() -> ecc_config:

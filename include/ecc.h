@@ -204,10 +204,13 @@ int ecc_stream_file(ecc_handle* h, const char* path, int64_t offset, const int64
 int ecc_compute_batch(ecc_handle* h, int n, const ecc_image* images, ecc_result* outs);
 
 /* Serving: queues one request. The image (host pointer, integer dtype) is
- * copied before the call returns. A scheduler thread admits queued requests
- * while their device memory fits under cfg->mem_cap_bytes, launches each
- * admitted group as one batched launch, and keeps launching newly admitted
- * groups while earlier ones run. A request whose image is larger than
+ * copied before the call returns (an image in pinned host memory straight to
+ * the device, the call waiting for that copy). A scheduler thread admits
+ * queued requests while their device memory fits under cfg->mem_cap_bytes,
+ * launches the requests whose copies have finished as one batched launch on
+ * one of two slots, and keeps launching while earlier batches run; with one
+ * batch in flight the next one waits to hold 32 requests or 64 M voxels, or
+ * until its oldest request has waited 200 us. A request whose image is larger than
  * cfg->ring_bytes is streamed instead (Sec. 3, "Streaming"): slabs of
  * dims[0] planes pass through a ring of at most cfg->ring_bytes under the
  * cap, one such request at a time, its partial VCEC kept on the device, while

@@ -33,7 +33,8 @@
  * exception ever crosses this boundary. ecc_last_error() gives a message.
  *
  * Threads: a handle may be used from one thread at a time, except that
- * ecc_submit / ecc_poll may be called concurrently from any threads.
+ * ecc_submit / ecc_submit_borrowed / ecc_poll may be called concurrently from
+ * any threads.
  */
 #ifndef ECC_GB300_H
 #define ECC_GB300_H

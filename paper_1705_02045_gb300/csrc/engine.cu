@@ -144,10 +144,13 @@ int stage_image(ecc_handle* h, const void* image, bool on_device, const Shape& s
 }
 
 // Host images of at least this many bytes are uploaded in plane chunks that
-// overlap with the computation (ecc_compute); at most kUploadChunksMax chunks.
+// overlap with the computation (ecc_compute): at most kUploadChunksMax equal
+// chunks, the last one then cut in halves.
 constexpr size_t kChunkedUploadBytes = size_t(16) << 20;
 constexpr int64_t kFusedScanBins = 2048;
 constexpr int64_t kUploadChunksMax = 16;
+constexpr size_t kUploadChunkBytes = size_t(32) << 20;
+constexpr size_t kUploadTailBytes = size_t(2) << 20;
 
 int enqueue_int(ecc_handle* h, const void* d_img, int64_t row_pitch, const Shape& s, int dtype,
                 int64_t bins, long long* d_vcec, long long* d_curve, cudaStream_t stream,
@@ -231,11 +234,14 @@ int enqueue_int(ecc_handle* h, const void* d_img, int64_t row_pitch, const Shape
           (e = cudaEventRecord(prof.a, stream)))
         return cuda_err(h, e, "profiling event");
     }
+    // chunk k's launches take its planes but the last (whose upper neighbour
+    // is the next chunk's first plane) and the previous chunk's last plane,
+    // so each waits only for its own chunk's copy
     const int K = n_chunks > 0 ? n_chunks : 1;
     for (int k = 0; k < K; ++k) {
-      const int64_t lo = n_chunks > 0 && k > 0 ? chunk_end[k - 1] : 0;
-      const int64_t hi = n_chunks > 0 ? chunk_end[k] : a.n[0];
-      if (n_chunks > 0 && (e = cudaStreamWaitEvent(stream, chunk_ev[std::min(k + 1, K - 1)], 0)))
+      const int64_t lo = n_chunks > 0 && k > 0 ? chunk_end[k - 1] - 1 : 0;
+      const int64_t hi = n_chunks > 0 && k < K - 1 ? chunk_end[k] - 1 : a.n[0];
+      if (n_chunks > 0 && (e = cudaStreamWaitEvent(stream, chunk_ev[k], 0)))
         return cuda_err(h, e, "wait upload");
       for (int64_t w = lo; w < hi; w += step) {
         a.w_lo = w;
@@ -559,8 +565,20 @@ int ecc_compute(ecc_handle* h, const void* image, const int64_t* dims, int ndim,
       // has arrived, so the copy and the computation overlap
       if ((e = h->img.ensure(bytes))) return cuda_err(h, e, "image buffer");
       const int64_t plane = (int64_t)(bytes / (size_t)s.n[0]);
-      const int K = (int)std::min<int64_t>(
-          {s.n[0], kUploadChunksMax, std::max<int64_t>(2, (int64_t)(bytes / kChunkedUploadBytes) * 4)});
+      const int Keq = (int)std::min<int64_t>(
+          {s.n[0], kUploadChunksMax, std::max<int64_t>(2, (int64_t)(bytes / kUploadChunkBytes))});
+      // equal chunks of about kUploadChunkBytes, the last one cut in halves
+      // down to about kUploadTailBytes: few copies (each has a fixed cost on
+      // the copy engine) and little work left once the copy has ended
+      std::vector<int64_t> ends;
+      for (int k = 1; k < Keq; ++k) ends.push_back(s.n[0] * k / Keq);
+      int64_t zt = ends.empty() ? 0 : ends.back();
+      while (s.n[0] - zt >= 2 && (size_t)(s.n[0] - zt) * (size_t)plane > kUploadTailBytes) {
+        zt += (s.n[0] - zt) / 2;
+        ends.push_back(zt);
+      }
+      ends.push_back(s.n[0]);
+      const int K = (int)ends.size();
       while ((int)h->up_ev.size() < K) {
         cudaEvent_t ev;
         if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming))) return cuda_err(h, e, "event");
@@ -572,10 +590,8 @@ int ecc_compute(ecc_handle* h, const void* image, const int64_t* dims, int ndim,
       if ((e = cudaEventRecord(h->up_free, h->stream)) ||
           (e = cudaStreamWaitEvent(h->copy_stream, h->up_free, 0)))
         return cuda_err(h, e, "order upload");
-      std::vector<int64_t> ends(K);
       for (int k = 0; k < K; ++k) {
-        const int64_t z0 = s.n[0] * k / K, z1 = s.n[0] * (k + 1) / K;
-        ends[k] = z1;
+        const int64_t z0 = k > 0 ? ends[k - 1] : 0, z1 = ends[k];
         char* dst = static_cast<char*>(h->img.p) + (size_t)(z0 * plane);
         const char* src = static_cast<const char*>(image) + (size_t)(z0 * plane);
         if ((e = cudaMemcpyAsync(dst, src, (size_t)((z1 - z0) * plane), cudaMemcpyHostToDevice,

@@ -482,3 +482,45 @@ def test_serve_borrowed_over_cap_and_streamed(lib):
         ecc.ecc_destroy(h)
     for img, g in zip(order, got):
         assert np.array_equal(g, oracle.ecc_int(img, 16384, "V"))
+
+
+def test_serve_borrowed_many_requests_two_threads(lib):
+    """300 borrowed requests from two threads: more than the copies the
+    library keeps in flight at a time (64), so submitters wait for room and
+    the request loop batches requests as their copies finish; every curve is
+    the oracle's and the binding has let go of every image."""
+    import threading
+    import torch
+    rng = np.random.default_rng(S + 120)
+    imgs = []
+    for i in range(300):
+        shape = tuple(int(x) for x in rng.integers(2, 24, size=int(rng.integers(1, 4))))
+        imgs.append(torch.from_numpy(synth.smooth_u8(shape, 1.0, S + 121 + i)).pin_memory())
+    h = ecc.ecc_create(device=0)
+    ids = [None] * len(imgs)
+    errors = []
+
+    def client(k):
+        try:
+            for i in range(k, len(imgs), 2):
+                ids[i] = ecc.ecc_submit_borrowed(h, imgs[i])
+        except Exception as e:  # pragma: no cover - reported below
+            errors.append(repr(e))
+
+    try:
+        threads = [threading.Thread(target=client, args=(k,)) for k in range(2)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        assert not errors, errors
+        got = []
+        for rid in ids:
+            st, curve = ecc.ecc_poll(h, rid, timeout_us=120_000_000)
+            assert st == ecc.ECC_OK
+            got.append(curve)
+        assert not [k for k in ecc._borrowed if k[0] == h.value]
+    finally:
+        ecc.ecc_destroy(h)
+    for t, g in zip(imgs, got):
+        assert np.array_equal(g, oracle.ecc_int(t.numpy(), 256, "V"))

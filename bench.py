@@ -180,7 +180,9 @@ def _oracle_planes(task):
 def oracle_on_host_cores(img, bins: int, seconds: float):
     """The oracle, as it stands, over plane ranges of the image on every host
     core (a spawned process pool: one process per core, the image in shared
-    memory). Returns (voxels, wall seconds, processes, planes per task)."""
+    memory), for about `seconds` of CPU work in all: one task of k planes per
+    process, in as many rounds as that takes. Returns (voxels, wall seconds,
+    processes, planes per task, rounds)."""
     import multiprocessing as mp
     from multiprocessing import shared_memory
     import oracle
@@ -191,11 +193,12 @@ def oracle_on_host_cores(img, bins: int, seconds: float):
     # planes per task so that one round of tasks (one per process) takes
     # about `seconds`, at most the whole image split over the processes
     k = int(max(1, min(img.shape[0] // procs or 1, seconds / one)))
+    rounds = int(max(1, min(16, round(seconds / (procs * k * one)))))
     shm = shared_memory.SharedMemory(create=True, size=img.nbytes)
     try:
         np.ndarray(img.shape, dtype=img.dtype, buffer=shm.buf)[...] = img
         tasks = [(shm.name, img.shape, img.dtype.str, bins, (i * k) % img.shape[0],
-                  (i * k) % img.shape[0] + k) for i in range(procs)]
+                  (i * k) % img.shape[0] + k) for i in range(procs)] * rounds
         with mp.get_context("spawn").Pool(procs) as pool:
             pool.map(_oracle_planes, [(shm.name, img.shape, img.dtype.str, bins, 0, 1)] * procs)
             t0 = time.perf_counter()
@@ -204,15 +207,16 @@ def oracle_on_host_cores(img, bins: int, seconds: float):
     finally:
         shm.close()
         shm.unlink()
-    return planes * img.shape[1] * img.shape[2], wall, procs, k
+    return planes * img.shape[1] * img.shape[2], wall, procs, k, rounds
 
 
 def cpu_baseline(img, seconds: float = 15.0):
     """The oracle on a bounded sample of the same image, on all host cores."""
-    vox, wall, procs, k = oracle_on_host_cores(img, BINS, seconds)
+    vox, wall, procs, k, rounds = oracle_on_host_cores(img, BINS, seconds)
     return {"value": vox / wall / 1e9, "unit": "Gvoxel/s", "cores": procs, "kind": "oracle",
-            "sample": f"{procs} processes x cells of {k} consecutive planes of the same 512^3 "
-                      f"image: {vox} voxels in {wall:.1f} s (numpy oracle, one process per "
+            "sample": f"{rounds} rounds of {procs} processes x cells of {k} consecutive planes "
+                      f"of the same 512^3 image: {vox} voxels in {wall:.1f} s "
+                      f"(~{wall * procs:.0f} s of CPU work; numpy oracle, one process per "
                       "host core)"}
 
 

@@ -30,6 +30,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <system_error>
 
 namespace ecc {
 
@@ -63,6 +64,8 @@ struct BHeader {
 };
 
 constexpr int kMaxBatch = 1024;
+constexpr size_t kParallelResultBytes = size_t(8) << 20;  // curves copied out by kResultThreads
+constexpr size_t kResultThreads = 4;
 constexpr int64_t kSmallBins = 256;
 constexpr int kBatchBitsWarps = 8;
 constexpr int kBatchPlRec = 17;  // odd and >= 16 + 1 planes
@@ -1516,11 +1519,33 @@ int ecc_compute_batch(ecc_handle* h, int n, const ecc_image* images, ecc_result*
       int rc = slot_run(h, sl, h->batch->tune, specs, nullptr);
       if (!rc) rc = wait_event(h, sl.done, 300LL * 1000 * 1000);
       if (rc) return rc;
-      for (size_t j = c0; j < c1; ++j) {
-        ecc_result& o = outs[idx[j]];
-        o.status = slot_result(sl, specs, (int)(j - c0), &o.curve);
-        o.bins = o.status == ECC_OK ? specs[j - c0].bins : 0;
+      // curves out of the pinned arena; many megabytes of them are split
+      // over a few threads (each curve its own allocation, as the caller
+      // frees them one by one)
+      auto take = [&](size_t a, size_t b) {
+        for (size_t j = a; j < b; ++j) {
+          ecc_result& o = outs[idx[j]];
+          o.status = slot_result(sl, specs, (int)(j - c0), &o.curve);
+          o.bins = o.status == ECC_OK ? specs[j - c0].bins : 0;
+        }
+      };
+      size_t res_bytes = 0;
+      for (const ImgSpec& sp : specs) res_bytes += sizeof(int64_t) * (size_t)sp.bins;
+      const size_t nt = res_bytes >= kParallelResultBytes ? kResultThreads : 1;
+      std::vector<std::thread> helpers;
+      size_t done_to = c0;
+      try {
+        for (size_t t = 1; t < nt; ++t) {
+          const size_t a = c0 + (c1 - c0) * t / nt, b = c0 + (c1 - c0) * (t + 1) / nt;
+          helpers.emplace_back(take, a, b);
+          done_to = b;
+        }
+      } catch (const std::system_error&) {
+        // no thread: this one copies the rest
       }
+      take(c0, helpers.empty() ? c1 : c0 + (c1 - c0) / nt);
+      for (std::thread& t : helpers) t.join();
+      if (done_to < c1 && !helpers.empty()) take(done_to, c1);
     }
     return ECC_OK;
   } catch (const std::bad_alloc&) {

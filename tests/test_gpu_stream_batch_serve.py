@@ -524,3 +524,27 @@ def test_serve_borrowed_many_requests_two_threads(lib):
         ecc.ecc_destroy(h)
     for t, g in zip(imgs, got):
         assert np.array_equal(g, oracle.ecc_int(t.numpy(), 256, "V"))
+
+
+def test_batch_many_large_histograms(lib):
+    """80 images with 16384 bins each (10.5 MB of curves, copied out of the
+    pinned arena by several threads) plus small ones: every curve is the
+    oracle's and lands in its own slot of the result list."""
+    rng = np.random.default_rng(S + 130)
+    imgs, bins = [], []
+    for i in range(100):
+        shape = tuple(int(x) for x in rng.integers(2, 14, size=int(rng.integers(1, 4))))
+        if i % 5 == 4:
+            imgs.append(synth.smooth_u8(shape, 1.0, S + 131 + i))
+            bins.append(256)
+        else:
+            imgs.append(synth.smooth_int(shape, 1.0, 16383, S + 131 + i, np.uint16))
+            bins.append(16384)
+    h = ecc.ecc_create(device=0)
+    try:
+        res = ecc.ecc_compute_batch(h, imgs, bins)
+    finally:
+        ecc.ecc_destroy(h)
+    assert len(res) == len(imgs)
+    for img, b, r in zip(imgs, bins, res):
+        assert np.array_equal(r, oracle.ecc_int(img, b, "V"))

@@ -204,9 +204,10 @@ int ecc_stream_file(ecc_handle* h, const char* path, int64_t offset, const int64
  * image i's curve and outs[i].status its status. Blocks until done. */
 int ecc_compute_batch(ecc_handle* h, int n, const ecc_image* images, ecc_result* outs);
 
-/* Serving: queues one request. The image (host pointer, integer dtype) is
- * copied before the call returns (an image in pinned host memory straight to
- * the device, the call waiting for that copy). A scheduler thread admits
+/* Serving: queues one request. The image (integer dtype; pageable or pinned
+ * host memory, or device memory of the handle's device) is copied before the
+ * call returns (pinned and device images straight to the device, the call
+ * waiting for that copy). A scheduler thread admits
  * queued requests while their device memory fits under cfg->mem_cap_bytes,
  * launches the requests whose copies have finished as one batched launch on
  * one of two slots, and keeps launching while earlier batches run; with one
@@ -221,7 +222,8 @@ int ecc_submit(ecc_handle* h, const void* image, const int64_t* dims, int ndim,
                ecc_dtype dtype, uint64_t* req_id);
 
 /* As ecc_submit, but an image in pinned host memory (cudaHostAlloc'd or
- * registered) is borrowed instead of copied before the call returns: its
+ * registered) or in device memory is borrowed instead of copied before the
+ * call returns: its
  * device copy is enqueued on the server's copy stream (ordered before the
  * request's batch) or, over the memory cap, made when the scheduler admits
  * the request, and a streamed request reads its slabs from it. The caller

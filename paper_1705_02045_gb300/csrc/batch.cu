@@ -876,9 +876,9 @@ bool admit(ecc_handle* h, Server* sv, Request* r) {
     const size_t dense = dtype_bytes(r->dtype) * (size_t)r->n[2];
     if ((size_t)r->pitch != dense)
       e = cudaMemcpy2DAsync(d, (size_t)r->pitch, r->src, dense, dense,
-                            (size_t)(r->n[0] * r->n[1]), cudaMemcpyHostToDevice, sv->copy_stream);
+                            (size_t)(r->n[0] * r->n[1]), cudaMemcpyDefault, sv->copy_stream);
     else
-      e = cudaMemcpyAsync(d, r->src, r->bytes, cudaMemcpyHostToDevice,
+      e = cudaMemcpyAsync(d, r->src, r->bytes, cudaMemcpyDefault,
                           sv->copy_stream);
     if (e) {
       cudaFreeAsync(d, sv->copy_stream);
@@ -1064,7 +1064,7 @@ bool job_step(ecc_handle* h, Server* sv, std::unique_lock<std::mutex>& lk) {
     const unsigned char* src = r->src + (size_t)j.next_z * r->plane_bytes;
     lk.unlock();
     e = cudaMemcpyAsync(base + r->plane_bytes, src, (size_t)cnz * r->plane_bytes,
-                        cudaMemcpyHostToDevice, sv->job_copy);
+                        cudaMemcpyDefault, sv->job_copy);
     lk.lock();
     if (e || (e = cudaEventRecord(j.copied[k], sv->job_copy)) ||
         (e = cudaStreamWaitEvent(sv->job_stream, j.copied[k], 0)))
@@ -1596,27 +1596,30 @@ static int submit_request(ecc_handle* h, const void* image, const int64_t* dims,
       delete r;
       return set_err(h, ECC_ERR_OOM, "request larger than the device memory cap");
     }
-    // Without borrowing, pinned host memory goes straight to the device if
-    // the cap allows and the call waits for that copy; otherwise the image
-    // is copied on the host. A borrowed pinned image is read in place: it is
-    // admitted like a host copy (by the scheduler, or here if there is room),
-    // its copy enqueued under the limit on copies in flight, and the request
-    // joins a batch once that copy's event has completed.
-    bool pinned = false;
+    // An image in pinned host memory or in device (or managed) memory goes
+    // straight to the request's device buffer by the copy engine if the cap
+    // allows; without borrowing the call waits for that copy. Otherwise a
+    // borrowed image is read in place later (admission, or the slabs of a
+    // streamed request) and any other is copied into host memory first.
+    // A borrowed request joins a batch once its copy's event has completed.
+    bool pinned = false, on_dev = false;
     if (r->bytes) {
       cudaPointerAttributes at{};
-      if (cudaPointerGetAttributes(&at, image) == cudaSuccess)
+      if (cudaPointerGetAttributes(&at, image) == cudaSuccess) {
         pinned = at.type == cudaMemoryTypeHost;
-      else
+        on_dev = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+      } else {
         cudaGetLastError();
+      }
     }
+    const bool direct = pinned || on_dev;  // copied asynchronously by the copy engine
     // The memory (and, when borrowing, a place in the window of copies in
     // flight) is reserved under the lock, the copy enqueued without it. A
     // borrowing caller whose window is full waits for the oldest copy in
     // flight, without the lock.
     cudaEvent_t copied = nullptr;  // the copy's completion event
     bool reserved = false;
-    if (pinned && !r->streamed) {
+    if (direct && !r->streamed) {
       const auto deadline = std::chrono::steady_clock::now() + std::chrono::seconds(300);
       std::unique_lock<std::mutex> lk(sv->mu);
       while (sv->bytes_in_use + request_cost(r) <= h->cfg.mem_cap_bytes) {
@@ -1648,7 +1651,7 @@ static int submit_request(ecc_handle* h, const void* image, const int64_t* dims,
       void* d = nullptr;
       cudaError_t e = cudaMallocAsync(&d, r->dev_bytes, sv->copy_stream);
       if (e == cudaSuccess &&
-          (e = cudaMemcpyAsync(d, image, r->bytes, cudaMemcpyHostToDevice, sv->copy_stream)) ==
+          (e = cudaMemcpyAsync(d, image, r->bytes, cudaMemcpyDefault, sv->copy_stream)) ==
               cudaSuccess &&
           (e = cudaEventRecord(copied, sv->copy_stream)) == cudaSuccess) {
         r->d_img = d;
@@ -1678,11 +1681,20 @@ static int submit_request(ecc_handle* h, const void* image, const int64_t* dims,
         return rc;
       }
     } else if (r->state != Request::kOnDevice) {
-      if (borrow && pinned) {
+      if (borrow && direct) {
         r->src = static_cast<const unsigned char*>(image);
       } else {
         r->host_copy.resize(r->bytes);
-        if (r->bytes) std::memcpy(r->host_copy.data(), image, r->bytes);
+        if (on_dev) {
+          const cudaError_t e =
+              cudaMemcpy(r->host_copy.data(), image, r->bytes, cudaMemcpyDefault);
+          if (e != cudaSuccess) {
+            delete r;
+            return cuda_err(h, e, "copy device image");
+          }
+        } else if (r->bytes) {
+          std::memcpy(r->host_copy.data(), image, r->bytes);
+        }
         r->src = r->host_copy.data();
       }
     }

@@ -548,3 +548,35 @@ def test_batch_many_large_histograms(lib):
     assert len(res) == len(imgs)
     for img, b, r in zip(imgs, bins, res):
         assert np.array_equal(r, oracle.ecc_int(img, b, "V"))
+
+
+@pytest.mark.parametrize("borrowed", [False, True])
+def test_serve_device_images(lib, borrowed):
+    """Requests whose images are CUDA tensors, through ecc_submit and
+    ecc_submit_borrowed: under a cap of a few requests (the rest wait for
+    admission), and two larger than the ring (streamed from device memory);
+    every curve is the oracle's."""
+    import torch
+    submit = ecc.ecc_submit_borrowed if borrowed else ecc.ecc_submit
+    small = [synth.smooth_u8((24, 64, 64), 2.0, S + 140 + i) for i in range(9)]
+    big3 = synth.two_phase_u16((60, 40, 130), 1.5, S + 150)
+    big2 = synth.smooth_int((700, 500), 2.0, 16383, S + 151, np.uint16)
+    order = small[:4] + [big3] + small[4:] + [big2]
+    one = 24 * 64 * 64 + 8 * (2 * 16384 + 1)
+    h = ecc.ecc_create(device=0, bins=16384, ring_bytes=256 * 1024, slab_depth=8,
+                       mem_cap_bytes=3 * one)
+    try:
+        dev = [torch.from_numpy(img.view(np.int16) if img.dtype == np.uint16 else img).cuda()
+               for img in order]
+        dev = [d.view(torch.uint16) if img.dtype == np.uint16 else d for d, img in zip(dev, order)]
+        torch.cuda.synchronize()
+        ids = [submit(h, d) for d in dev]
+        got = []
+        for rid in ids:
+            st, curve = ecc.ecc_poll(h, rid, timeout_us=120_000_000)
+            assert st == ecc.ECC_OK
+            got.append(curve)
+    finally:
+        ecc.ecc_destroy(h)
+    for img, g in zip(order, got):
+        assert np.array_equal(g, oracle.ecc_int(img, 16384, "V"))

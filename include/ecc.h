@@ -171,8 +171,8 @@ int ecc_stream_begin(ecc_handle* h, const int64_t* dims, int ndim, ecc_dtype dty
                      ecc_stream** out);
 
 /* Pushes planes [z0, z0 + nz) of the image (host memory, pinned for full
- * copy speed; C order, dims of one plane as given to ecc_stream_begin).
- * Returns once the host buffer may be reused; the computation continues in
+ * copy speed, or device memory; C order, dims of one plane as given to
+ * ecc_stream_begin). Returns once the buffer may be reused; the computation continues in
  * the background. Errors: ECC_ERR_STATE (z0 not the next plane, after finish),
  * ECC_ERR_ARG, ECC_ERR_CUDA. */
 int ecc_stream_push_slab(ecc_stream* s, const void* host_planes, int64_t z0, int64_t nz);

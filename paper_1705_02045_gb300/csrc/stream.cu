@@ -221,10 +221,10 @@ int ecc_stream_push_slab(ecc_stream* st, const void* host_planes, int64_t z0, in
       if (st->row_pitch)
         e = cudaMemcpy2DAsync(base + st->plane_bytes, (size_t)st->row_pitch, src + off * src_plane,
                               st->src_row, st->src_row, cnz * st->rows_per_plane,
-                              cudaMemcpyHostToDevice, h->copy_stream);
+                              cudaMemcpyDefault, h->copy_stream);
       else
         e = cudaMemcpyAsync(base + st->plane_bytes, src + off * src_plane, cnz * src_plane,
-                            cudaMemcpyHostToDevice, h->copy_stream);
+                            cudaMemcpyDefault, h->copy_stream);
       if (e ||
           (e = cudaEventRecord(sl.copied, h->copy_stream)) ||
           (e = cudaStreamWaitEvent(h->stream, sl.copied, 0)))

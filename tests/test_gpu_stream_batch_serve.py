@@ -103,6 +103,28 @@ def test_stream_pinned_host_buffer(lib):
     assert np.array_equal(got, oracle.ecc_int(img, 256, "V"))
 
 
+def test_stream_device_slabs(lib):
+    """Slabs pushed from device memory (a CUDA tensor reused for every slab,
+    as the call returns once its copies are done), 14-bit values, uneven
+    slabs; the curve is the oracle's."""
+    import torch
+    img = synth.two_phase_u16((23, 40, 70), 1.5, S + 6)
+    h = ecc.ecc_create(device=0, bins=16384, slab_depth=4)
+    try:
+        s = ecc.ecc_stream_begin(h, img.shape, img.dtype)
+        buf = torch.empty((7, 40, 70), dtype=torch.int16, device="cuda")
+        z = 0
+        for n in (7, 3, 7, 6):
+            buf[:n].copy_(torch.from_numpy(img[z:z + n].view(np.int16)))
+            torch.cuda.synchronize()
+            ecc.ecc_stream_push_slab(h, s, buf[:n].view(torch.uint16), z)
+            z += n
+        got = ecc.ecc_stream_finish(h, s)
+    finally:
+        ecc.ecc_destroy(h)
+    assert np.array_equal(got, oracle.ecc_int(img, 16384, "V"))
+
+
 def test_stream_errors(lib):
     img = synth.uniform_u8((10, 8, 8), S + 6)
     h = ecc.ecc_create(device=0, slab_depth=4)

@@ -149,8 +149,11 @@ class _ResultOwner:
         C.memmove(C.byref(self.r), C.byref(r), C.sizeof(ecc_result))
 
     def __del__(self):
-        if _lib is not None:
-            _lib.ecc_result_free(C.byref(self.r))
+        try:
+            if _lib is not None:
+                _lib.ecc_result_free(C.byref(self.r))
+        except Exception:  # interpreter shutdown: the process frees everything
+            pass
 
 
 def _view(owner, ptr, n: int, ctype, dtype):

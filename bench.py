@@ -823,7 +823,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u8", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "global_batch": world, "voxels_per_gpu": nvox,
+            "config": {"workload": WORKLOAD, "images": world, "voxels_per_gpu": nvox,
                        "bins": BINS, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "256 MiB write between steps, outside the timed events"},
             "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak,

@@ -69,6 +69,7 @@ constexpr size_t kResultThreads = 4;
 constexpr int64_t kSmallBins = 256;
 constexpr int kBatchBitsWarps = 8;
 constexpr int kBatchPlRec = 17;  // odd and >= 16 + 1 planes
+constexpr int kBatchMinDepth = 4;  // planes per tile of the thinnest batched tiles
 constexpr int kGrabPerBlock = 4;  // bit-sliced work-list chunks per persistent block
 
 namespace {
@@ -488,7 +489,25 @@ int slot_run(ecc_handle* h, Slot& sl, BatchTune& tune, const std::vector<ImgSpec
              cudaEvent_t wait_ev, unsigned char* h_res = nullptr) {
   cudaError_t e;
   const int n = (int)specs.size();
-  const int depth = tune_depth(tune, sl);
+  int depth = tune_depth(tune, sl);
+  // A batch too small to give every block a tile at that depth takes thinner
+  // tiles (more of them, each with one priming plane more), down to
+  // kBatchMinDepth planes: a lone small request then runs on many blocks
+  // instead of marching through all its planes on a few. Such a batch is not
+  // used to tune the depth.
+  auto bits_tiles = [&](int64_t d) {
+    int64_t t = 0;
+    for (const ImgSpec& sp : specs) {
+      if (sp.n[0] * sp.n[1] * sp.n[2] == 0 || !image_nb(h, sp)) continue;
+      const int64_t zc = std::min<int64_t>(d, std::max<int64_t>(sp.n[0], 1));
+      t += bits_geo(sp.n[2], sp.n[1], sp.n[0], kBatchBitsWarps, zc).n_tiles;
+    }
+    return t;
+  };
+  if (tune.fixed == 0 && bits_tiles(depth) < sl.L.grid_b) {
+    while (depth > kBatchMinDepth && bits_tiles(depth) < sl.L.grid_b) depth /= 2;
+    sl.tune_cand = -1;
+  }
   double bits_vox = 0;
   bool large = false;
   // device arena: all VCECs, then all (curve, error word) records, so that

@@ -70,6 +70,7 @@ constexpr int64_t kSmallBins = 256;
 constexpr int kBatchBitsWarps = 8;
 constexpr int kBatchPlRec = 17;  // odd and >= 16 + 1 planes
 constexpr int kBatchMinDepth = 4;  // planes per tile of the thinnest batched tiles
+constexpr int kZeroThreads = 1024;  // threads clearing one image's VCEC
 constexpr int kGrabPerBlock = 4;  // bit-sliced work-list chunks per persistent block
 
 namespace {
@@ -237,11 +238,22 @@ k_batch_bits(unsigned char* __restrict__ desc, DescLayout L) {
   if (cur >= 0) flush_bits_hist(imgs[cur], hist);
 }
 
-__global__ void k_batch_zero(const unsigned char* __restrict__ desc, DescLayout L) {
+// Clears image blockIdx.x's VCEC (16-byte stores where it is 16-byte
+// aligned) and error word.
+__global__ void __launch_bounds__(kZeroThreads)
+k_batch_zero(const unsigned char* __restrict__ desc, DescLayout L) {
   const BHeader* hdr = reinterpret_cast<const BHeader*>(desc + L.hdr);
   if ((int)blockIdx.x >= hdr->n_images) return;
   const BImage& im = reinterpret_cast<const BImage*>(desc + L.imgs)[blockIdx.x];
-  for (int64_t b = threadIdx.x; b < im.bins; b += blockDim.x) im.vcec[b] = 0;
+  long long* v = im.vcec;
+  int64_t b0 = 0;
+  if ((reinterpret_cast<uintptr_t>(v) & 15u) == 0) {
+    longlong2* v2 = reinterpret_cast<longlong2*>(v);
+    const int64_t n2 = im.bins / 2;
+    for (int64_t i = threadIdx.x; i < n2; i += blockDim.x) v2[i] = make_longlong2(0, 0);
+    b0 = 2 * n2;
+  }
+  for (int64_t b = b0 + threadIdx.x; b < im.bins; b += blockDim.x) v[b] = 0;
   if (threadIdx.x == 0) *im.err = 0;
 }
 
@@ -324,7 +336,7 @@ cudaError_t capture_graph(Slot& sl, bool large, cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   unsigned char* d = sl.desc.as<unsigned char>();
   if ((e = cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal))) return e;
-  k_batch_zero<<<kMaxBatch, 256, 0, sl.stream>>>(d, sl.L);
+  k_batch_zero<<<kMaxBatch, kZeroThreads, 0, sl.stream>>>(d, sl.L);
   if (large) {
     k_batch_bits<CONV, kSmemBinsMax><<<sl.L.grid_b, 32 * kBatchBitsWarps,
                                        bits_smem<kSmemBinsMax>(), sl.stream>>>(d, sl.L);

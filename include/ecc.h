@@ -127,7 +127,9 @@ void ecc_result_free(ecc_result* r);
 
 /* ECC of one image (Sec. 3, Algorithm 1 then "Post-Processing"). Blocks until
  * the result is in *out (host memory, owned by the library). A dimension of 0
- * gives the empty complex: an all-zero curve / no pairs. Errors: ECC_ERR_ARG,
+ * gives the empty complex: an all-zero curve / no pairs. A device image must
+ * be aligned to its element size (host images may start anywhere). Errors:
+ * ECC_ERR_ARG,
  * ECC_ERR_DTYPE, ECC_ERR_VALUE (value >= bins, NaN/Inf), ECC_ERR_OOM,
  * ECC_ERR_CUDA. */
 int ecc_compute(ecc_handle* h, const void* image, const int64_t* dims, int ndim,
@@ -135,7 +137,8 @@ int ecc_compute(ecc_handle* h, const void* image, const int64_t* dims, int ndim,
 
 /* Same for an integer image already on the device, enqueued on `stream`
  * (a cudaStream_t; NULL = the handle's stream) without any host
- * synchronisation. d_curve: device int64[bins], written by the call. The
+ * synchronisation. d_image must be aligned to its element size (else
+ * ECC_ERR_ARG). d_curve: device int64[bins], written by the call. The
  * library's device scratch is shared by all calls on the handle, so calls on
  * different streams must not overlap. Out-of-range values are not
  * reported by this call: ecc_device_status() reports them. */
@@ -269,12 +272,16 @@ int ecc_profile_read(ecc_handle* h, double* contrib_ms, int64_t* count);
  * that loads the library until the process exits. Hence bins must lie in
  * 1..65536; a larger bins returns ECC_ERR_ARG.
  *
- * d_image: device image of the current device, layout as everywhere in this
- * header (ECC_U8 or ECC_U16, 1 <= ndim <= 4). convention: ECC_CONV_V or
- * ECC_CONV_T. d_curve: device int64[bins], written with chi(K_t). stream: a
- * cudaStream_t (NULL = the legacy default stream); the call enqueues its work
- * there and waits for it before returning. Errors: ECC_ERR_ARG, ECC_ERR_DTYPE,
- * ECC_ERR_VALUE (a value >= bins), ECC_ERR_CUDA.
+ * d_image: device (or managed) memory of the current device, layout as
+ * everywhere in this header (ECC_U8 or ECC_U16, 1 <= ndim <= 4), its address
+ * a multiple of the element size. convention: ECC_CONV_V or ECC_CONV_T.
+ * d_curve: device int64[bins] of the current device, 8-byte aligned, written
+ * with chi(K_t). stream: a cudaStream_t (NULL = the legacy default stream);
+ * the call enqueues its work there, copies the error word back and
+ * synchronises the stream before returning, also when it fails after
+ * enqueueing. Errors: ECC_ERR_ARG (also for a pointer that is not device
+ * memory of the current device, or misaligned), ECC_ERR_DTYPE, ECC_ERR_VALUE
+ * (a value >= bins), ECC_ERR_CUDA.
  *
  * The first call on a device (with that device current) looks up the
  * arrays' device address; make that first call before any stream capture.

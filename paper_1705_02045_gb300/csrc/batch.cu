@@ -494,6 +494,14 @@ int tune_depth(BatchTune& t, Slot& sl) {
   return BatchTune::kDepth[sl.tune_cand];
 }
 
+// A batch that does not take part in the depth tuning gives its candidate
+// back, so the rotation skips none.
+void untune_depth(BatchTune& t, Slot& sl) {
+  if (sl.tune_cand < 0) return;
+  t.next = sl.tune_cand;
+  sl.tune_cand = -1;
+}
+
 // h_res: pinned destination of the (curve, error word) records, at the
 // offsets sl.res_off (results_bytes(specs) bytes); null = the slot's own
 // pinned arena.
@@ -518,7 +526,7 @@ int slot_run(ecc_handle* h, Slot& sl, BatchTune& tune, const std::vector<ImgSpec
   };
   if (tune.fixed == 0 && bits_tiles(depth) < sl.L.grid_b) {
     while (depth > kBatchMinDepth && bits_tiles(depth) < sl.L.grid_b) depth /= 2;
-    sl.tune_cand = -1;
+    untune_depth(tune, sl);
   }
   double bits_vox = 0;
   bool large = false;
@@ -1518,6 +1526,11 @@ int ecc_compute_batch(ecc_handle* h, int n, const ecc_image* images, ecc_result*
       // images are read in place (the kernels take rows at any alignment)
       const int64_t pitch = staged_pitch(h, im.dtype, bins, sp.n[2]);
       const bool dev = is_device_ptr(h, im.data);
+      if (dev && !elem_aligned(im.data, im.dtype)) {
+        outs[i].status = set_err(h, ECC_ERR_ARG, "device image not aligned to its element size");
+        ok[i] = 0;
+        continue;
+      }
       if (!dev) {
         sp.row_pitch = pitch;
         stage_off[i] = staged;

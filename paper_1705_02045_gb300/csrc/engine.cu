@@ -531,6 +531,8 @@ int ecc_compute(ecc_handle* h, const void* image, const int64_t* dims, int ndim,
     cudaError_t e = cudaSetDevice(h->device);
     if (e) return cuda_err(h, e, "set device");
     const bool on_dev = s.voxels > 0 && is_device_ptr(h, image);
+    if (on_dev && !elem_aligned(image, dtype))
+      return set_err(h, ECC_ERR_ARG, "device image not aligned to its element size");
     if ((e = cudaMemsetAsync(h->errw.p, 0, sizeof(int), h->stream)))
       return cuda_err(h, e, "memset");
     if (dtype == ECC_F32) {
@@ -653,6 +655,8 @@ int ecc_compute_device(ecc_handle* h, const void* d_image, const int64_t* dims, 
     if (bins > (int64_t(1) << 24)) return set_err(h, ECC_ERR_ARG, "bins too large");
     if (!d_curve || (s.voxels > 0 && !d_image))
       return set_err(h, ECC_ERR_ARG, "null device pointer");
+    if (s.voxels > 0 && !elem_aligned(d_image, dtype))
+      return set_err(h, ECC_ERR_ARG, "device image not aligned to its element size");
     cudaError_t e = cudaSetDevice(h->device);
     if (e) return cuda_err(h, e, "set device");
     if ((e = h->vcec.ensure(sizeof(long long) * bins))) return cuda_err(h, e, "vcec buffer");
@@ -697,7 +701,10 @@ int ecc_compute_quantized(ecc_handle* h, const float* image, const int64_t* dims
       return cuda_err(h, e, "buffers");
     if ((e = cudaMemsetAsync(h->errw.p, 0, sizeof(int), h->stream))) return cuda_err(h, e, "memset");
     const float* d_in = image;
-    if (s.voxels > 0 && !is_device_ptr(h, image)) {
+    const bool in_dev = s.voxels > 0 && is_device_ptr(h, image);
+    if (in_dev && !elem_aligned(image, ECC_F32))
+      return set_err(h, ECC_ERR_ARG, "device image not aligned to its element size");
+    if (s.voxels > 0 && !in_dev) {
       if ((e = h->img.ensure(sizeof(float) * s.voxels))) return cuda_err(h, e, "image buffer");
       if ((e = cudaMemcpyAsync(h->img.p, image, sizeof(float) * s.voxels,
                                cudaMemcpyHostToDevice, h->stream)))

@@ -122,6 +122,11 @@ int validate_shape(ecc_handle* h, const int64_t* dims, int ndim, Shape* s);
 int64_t default_bins(const ecc_handle* h, int dtype);
 size_t dtype_bytes(int dtype);
 bool is_device_ptr(const ecc_handle* h, const void* p);
+// A device image is read with loads of its element type: its address must be
+// a multiple of the element size (host images are copied, so any address).
+inline bool elem_aligned(const void* p, int dtype) {
+  return (reinterpret_cast<uintptr_t>(p) % dtype_bytes(dtype)) == 0;
+}
 // Enqueues VCEC accumulation (zeroed first) + contribution kernel + scan of
 // an integer image already on the device.
 // With n_chunks > 0 the image is still arriving in plane chunks: planes

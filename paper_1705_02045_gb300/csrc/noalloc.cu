@@ -49,6 +49,17 @@ int scratch_for(int dev, DeviceScratch* out) {
   return ECC_OK;
 }
 
+// Device or managed memory of device dev.
+bool on_device(const void* p, int dev) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) &&
+         at.device == dev;
+}
+
 }  // namespace
 
 }  // namespace ecc
@@ -68,13 +79,28 @@ extern "C" int ecc_compute_device_noalloc(const void* d_image, const int64_t* di
     if (!d_curve || (s.voxels > 0 && !d_image)) return ECC_ERR_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ECC_ERR_CUDA;
+    // both buffers must be device (or managed) memory of the current device,
+    // and the image aligned to its element size (the kernels read whole
+    // elements)
+    if (!on_device(d_curve, dev) || (s.voxels > 0 && !on_device(d_image, dev)))
+      return ECC_ERR_ARG;
+    if (s.voxels > 0 && !elem_aligned(d_image, dtype)) return ECC_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(d_curve) & 7u) != 0) return ECC_ERR_ARG;
     DeviceScratch sc;
     if ((rc = scratch_for(dev, &sc))) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // Once anything is queued, an error return first waits for the stream, so
+    // that no kernel of a failed call is still writing the shared arrays when
+    // the next call starts.
+    auto fail = [&](int code) {
+      cudaStreamSynchronize(st);
+      cudaGetLastError();
+      return code;
+    };
     // the arrays keep the previous call's contents: clear what starts at zero
     if (cudaMemsetAsync(sc.vcec, 0, sizeof(long long) * bins, st) != cudaSuccess ||
         cudaMemsetAsync(sc.err, 0, sizeof(int), st) != cudaSuccess)
-      return ECC_ERR_CUDA;
+      return fail(ECC_ERR_CUDA);
     int64_t launches = 0;
     if (s.voxels > 0) {
       LocalArgs a;
@@ -93,16 +119,16 @@ extern "C" int ecc_compute_device_noalloc(const void* d_image, const int64_t* di
       for (int64_t w = 0; w < a.n[0]; w += step) {
         a.w_lo = w;
         a.w_hi = std::min(a.n[0], w + step);
-        if (launch_local(a, sc.num_sms, &launches) != cudaSuccess) return ECC_ERR_CUDA;
+        if (launch_local(a, sc.num_sms, &launches) != cudaSuccess) return fail(ECC_ERR_CUDA);
       }
     }
     if (launch_scan(sc.vcec, reinterpret_cast<long long*>(d_curve), bins, st, &launches) !=
         cudaSuccess)
-      return ECC_ERR_CUDA;
+      return fail(ECC_ERR_CUDA);
     int word = 0;
-    if (cudaMemcpyAsync(&word, sc.err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
-      return ECC_ERR_CUDA;
+    if (cudaMemcpyAsync(&word, sc.err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      return fail(ECC_ERR_CUDA);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return ECC_ERR_CUDA;
     if (word & kErrValue) return ECC_ERR_VALUE;
     if (word & kErrOverflow) return ECC_ERR_CUDA;
     return ECC_OK;

@@ -1,13 +1,15 @@
 """The allocation-free entry point (ecc_compute_device_noalloc), for callers that
-cannot allocate device memory: its curves must equal those of the regular
-device entry point (ecc_compute_device) exactly -- the curve is integer -- on
-two calls in a row, since the second call reuses the scratch the first one left
+cannot allocate device memory. Its curves must equal the oracle's element by
+element -- the curve is integer, so exactly -- in both cell conventions, and
+equal those of the regular device entry point (ecc_compute_device), on two
+calls in a row, since the second call reuses the scratch the first one left
 behind. Runs alone in a fresh process as well as after the other tests."""
 import ctypes as C
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_1705_02045_gb300 import ecc, synth
 
 pytestmark = pytest.mark.gpu
@@ -23,13 +25,17 @@ CASES = [
      lambda s: synth.uniform_int(s, 65536, synth.SEED_BASE + 74, np.uint16)),
 ]
 
+CONV_NAME = {ecc.ECC_CONV_V: "V", ecc.ECC_CONV_T: "T"}
+
 
 @pytest.mark.parametrize("conv", [ecc.ECC_CONV_V, ecc.ECC_CONV_T])
 @pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}-{np.dtype(c[1]).name}")
-def test_noalloc_equals_compute_device_twice(case, conv):
+def test_noalloc_equals_oracle_and_compute_device_twice(case, conv):
     import torch
     shape, dtype, bins, gen = case
-    img = torch.from_numpy(gen(shape).astype(dtype)).cuda()
+    host = gen(shape).astype(dtype)
+    expect = oracle.ecc_int(host, bins, CONV_NAME[conv])
+    img = torch.from_numpy(host).cuda()
     h = ecc.ecc_create(device=0, convention=conv)
     try:
         want = torch.empty(bins, dtype=torch.int64, device="cuda")
@@ -38,9 +44,11 @@ def test_noalloc_equals_compute_device_twice(case, conv):
         assert ecc.ecc_device_status(h) == ecc.ECC_OK
     finally:
         ecc.ecc_destroy(h)
+    assert np.array_equal(want.cpu().numpy(), expect)
     for _ in range(2):
         got = torch.full((bins,), -7, dtype=torch.int64, device="cuda")
         assert ecc.ecc_compute_device_noalloc(img, bins, got, convention=conv) == ecc.ECC_OK
+        assert np.array_equal(got.cpu().numpy(), expect)
         assert torch.equal(got, want)
 
 
@@ -57,6 +65,22 @@ def test_noalloc_limits_and_errors():
     # float images are not taken
     f = torch.zeros((4, 4), dtype=torch.float32, device="cuda")
     assert ecc.ecc_compute_device_noalloc(f, 256, curve) == ecc.ECC_ERR_DTYPE
+    # rejected before anything is enqueued: a uint16 image at an odd address,
+    # a host image, a host curve
+    raw = torch.zeros(2 * 64 + 2, dtype=torch.uint8, device="cuda")
+    dims = (C.c_int64 * 1)(64)
+    assert lib.ecc_compute_device_noalloc(C.c_void_p(raw.data_ptr() + 1), dims, 1, ecc.ECC_U16,
+                                          256, ecc.ECC_CONV_V, C.c_void_p(curve.data_ptr()),
+                                          None) == ecc.ECC_ERR_ARG
+    host = np.zeros(64, np.uint8)
+    assert lib.ecc_compute_device_noalloc(host.ctypes.data_as(C.c_void_p), dims, 1, ecc.ECC_U8,
+                                          256, ecc.ECC_CONV_V, C.c_void_p(curve.data_ptr()),
+                                          None) == ecc.ECC_ERR_ARG
+    host_curve = np.zeros(256, np.int64)
+    assert lib.ecc_compute_device_noalloc(C.c_void_p(raw.data_ptr()), dims, 1, ecc.ECC_U8,
+                                          256, ecc.ECC_CONV_V,
+                                          host_curve.ctypes.data_as(C.c_void_p),
+                                          None) == ecc.ECC_ERR_ARG
     # the next good call is unaffected by the failed ones
     img[1, 2, 3] = 0
     assert ecc.ecc_compute_device_noalloc(img, 256, curve) == ecc.ECC_OK

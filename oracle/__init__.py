@@ -24,6 +24,9 @@ from .ecc_oracle import (  # noqa: F401
     ecc_int,
     ecc_from_vcec,
     ecc_pairs_float,
+    vcec_float_zrange,
+    merge_vcec_float,
+    pairs_from_vcec_float,
     quantize_f32,
     ecc_quantized,
     cell_counts,

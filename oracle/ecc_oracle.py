@@ -229,6 +229,82 @@ def ecc_pairs_float(img: np.ndarray, convention: str = "V"):
     return t[keep].astype(np.float32), np.cumsum(a[keep], dtype=np.int64)
 
 
+def _chunk_voxel_planes(n0: int, lo: int, hi: int, convention: str):
+    """Voxel planes [p0, p1) along axis 0 that contain the cells whose axis-0
+    coordinate lies in [lo, hi): for V a singleton {b} lies in voxels b - 1
+    and b, an interval [a, a + 1] in voxel a; for T a point a is voxel a and
+    an edge [a, a + 1] joins voxels a and a + 1."""
+    if convention == "V":
+        return max(lo - 1, 0), min(hi, n0)
+    return lo, min(hi + 1, n0)
+
+
+def vcec_float_zrange(img: np.ndarray, lo: int, hi: int | None,
+                      convention: str = "V"):
+    """Float VCEC of the cells whose axis-0 coordinate lies in [lo, hi): the
+    distinct values of those cells, ascending (float64), and the signed count
+    sum (-1)^dim of the cells at each value, entries of count 0 left out.
+
+    This is the hash map of Sec. 3 ("Other Ranges of Gray Values") restricted
+    to one chunk of the partition of Sec. 3 ("Streaming"): the maps of a
+    partition of the axis-0 coordinates, merged by value
+    (`merge_vcec_float`), give the whole image's map.
+
+    Every cell value is the value of one of the voxels the chunk's cells
+    contain (the minimum of some of them for V, the maximum for T). Those
+    voxels' values are first replaced by their rank among the distinct values
+    present, a strictly increasing relabelling, with which minimum and maximum
+    commute; the integer VCEC of the rank image (`vcec_int_zrange`, bins = the
+    number of distinct values) is then the float map indexed by rank.
+    """
+    if img.dtype.kind != "f":
+        raise TypeError("float image expected")
+    n0 = img.shape[0]
+    top = n0 + 1 if convention == "V" else n0  # one past the last axis-0 coordinate
+    if convention not in ("V", "T"):
+        raise ValueError(f"unknown convention {convention!r}")
+    hi = top if hi is None else min(hi, top)
+    lo = max(lo, 0)
+    if img.size == 0 or lo >= hi:
+        return np.zeros(0, np.float64), np.zeros(0, np.int64)
+    p0, p1 = _chunk_voxel_planes(n0, lo, hi, convention)
+    vals, _ = _exact_values(img[p0:p1])
+    u, rank = np.unique(vals.ravel(), return_inverse=True)
+    rank = rank.reshape(vals.shape).astype(np.int32)
+    a = vcec_int_zrange(rank, len(u), lo - p0, hi - p0, convention)
+    keep = a != 0
+    return u[keep], a[keep]
+
+
+def merge_vcec_float(parts):
+    """Sum of float VCEC maps given as (values, counts) pairs: counts at equal
+    values add up (Sec. 3, "Post-Processing": the partial VCECs are summed);
+    values whose sum is 0 are left out."""
+    parts = list(parts)
+    if not parts:
+        return np.zeros(0, np.float64), np.zeros(0, np.int64)
+    k = np.concatenate([np.asarray(p[0], np.float64) for p in parts])
+    w = np.concatenate([np.asarray(p[1], np.int64) for p in parts])
+    if k.size == 0:
+        return k, w
+    order = np.argsort(k, kind="stable")
+    k, w = k[order], w[order]
+    starts = np.flatnonzero(np.r_[True, k[1:] != k[:-1]])
+    a = np.add.reduceat(w, starts)
+    t = k[starts]
+    keep = a != 0
+    return t[keep], a[keep]
+
+
+def pairs_from_vcec_float(values: np.ndarray, a: np.ndarray):
+    """(t, chi(K_t)) at every value t with a_t != 0, ascending: the running
+    sum of the map (Sec. 3, "Post-Processing"). Returns (float32, int64)."""
+    values = np.asarray(values, np.float64)
+    a = np.asarray(a, np.int64)
+    keep = a != 0
+    return values[keep].astype(np.float32), np.cumsum(a[keep], dtype=np.int64)
+
+
 def quantize_f32(img: np.ndarray, lo: float, hi: float, bins: int) -> np.ndarray:
     """The value transform of Sec. 3 ("Other Ranges of Gray Values": shift,
     scale, round into {0..m-1}), in the reading used here:

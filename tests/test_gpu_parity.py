@@ -127,6 +127,50 @@ def test_4d_several_x_tiles(hV, hT, conv, shape, kind):
         assert np.array_equal(t, t_ref) and np.array_equal(chi, chi_ref)
 
 
+@pytest.mark.parametrize("conv", ["V", "T"])
+def test_f32_4d_full_size_equals_oracle(tmp_path, conv):
+    """The 128^4 float field of the benchmark (Gaussian random field, sigma = 3
+    per axis), element by element against the oracle over the whole image:
+    every (threshold, chi) pair, computed on the host cores in chunks of 8
+    planes whose maps are merged by value."""
+    import oracle_pool
+    d = synth.grf_f32_torch((128, 128, 128, 128), 3.0, synth.SEED_BASE + 4).contiguous()
+    h = ecc.ecc_create(device=0, convention=ecc.ECC_CONV_V if conv == "V" else ecc.ECC_CONV_T)
+    try:
+        t, chi = ecc.ecc_compute(h, d)
+    finally:
+        ecc.ecc_destroy(h)
+    host = d.cpu().numpy()
+    del d
+    path = tmp_path / "grf4.raw"
+    host.tofile(path)
+    t_ref, chi_ref = oracle_pool.ecc_pairs_float_parallel(path, host.shape, 8, conv=conv)
+    assert len(t) == len(t_ref)
+    assert np.array_equal(t, t_ref) and np.array_equal(chi, chi_ref)
+
+
+@pytest.mark.parametrize("conv", ["V", "T"])
+def test_f32_4d_noise_past_1024_radix_tiles(tmp_path, conv):
+    """4D i.i.d. uniform floats, 64^4: more than half the voxels carry a
+    non-zero change, so the (key, change) pairs exceed 1024 radix tiles of
+    4096 and the digit offsets carry across tile chunks, and the segment and
+    non-zero compactions run on many blocks. Element by element against the
+    oracle."""
+    import oracle_pool
+    shape = (64, 64, 64, 64)
+    img = np.random.default_rng(S + 58).random(size=shape, dtype=np.float32)
+    h = ecc.ecc_create(device=0, convention=ecc.ECC_CONV_V if conv == "V" else ecc.ECC_CONV_T)
+    try:
+        t, chi = ecc.ecc_compute(h, img)
+    finally:
+        ecc.ecc_destroy(h)
+    path = tmp_path / "noise4.raw"
+    img.tofile(path)
+    t_ref, chi_ref = oracle_pool.ecc_pairs_float_parallel(path, shape, 4, conv=conv)
+    assert len(t_ref) > 1024 * 4096
+    assert np.array_equal(t, t_ref) and np.array_equal(chi, chi_ref)
+
+
 def test_f32_4d_full_size_properties(lib):
     """The 128^4 float field of the benchmark: thresholds strictly
     ascending, chi = 1 at the top (the full box is contractible), and the

@@ -253,6 +253,51 @@ def test_float_monotone_transform(conv, shape):
     assert chi.tolist() == e[nz].tolist()
 
 
+def _float_chunk_pin(conv, shape, seed):
+    """Sec. 3 ("Streaming" with "Other Ranges of Gray Values"): the float maps
+    of the chunks of any partition of the axis-0 coordinates, merged by value,
+    give the whole image's pairs as the plain per-cell-type enumeration
+    (`ecc_pairs_float`) computes them. Values repeat (ties across chunks)."""
+    rng = np.random.default_rng(seed)
+    img = rng.normal(size=shape).astype(np.float32)
+    flat = img.reshape(-1)
+    flat[rng.integers(0, flat.size, size=flat.size // 3)] = flat[0]  # ties
+    flat[rng.integers(0, flat.size, size=2)] = -0.0
+    want_t, want_chi = oracle.ecc_pairs_float(img, conv)
+    n0 = shape[0]
+    top = n0 + 1 if conv == "V" else n0
+    cuts = sorted(set([0, top] + [int(x) for x in rng.integers(0, top + 1, size=3)]))
+    for cc in (cuts, [0, top], list(range(top + 1))):
+        parts = [oracle.vcec_float_zrange(img, lo, hi, conv) for lo, hi in zip(cc[:-1], cc[1:])]
+        t, chi = oracle.pairs_from_vcec_float(*oracle.merge_vcec_float(parts))
+        assert t.tolist() == want_t.tolist()
+        assert chi.tolist() == want_chi.tolist()
+
+
+@pytest.mark.parametrize("conv", CONVS)
+@pytest.mark.parametrize("shape", [(13,), (9, 7), (6, 5, 7), (5, 4, 3, 4), (1, 3, 3), (2, 1, 4, 3)])
+def test_float_chunk_additivity(conv, shape):
+    _float_chunk_pin(conv, shape, 17)
+
+
+@pytest.mark.parametrize("name", ["lower collar plane dropped", "upper collar plane dropped"])
+def test_planted_float_chunk_mistake_is_caught(name, monkeypatch):
+    """A chunk that misses the voxel plane below (V) or above (T) its cells
+    gets the values of its boundary cells wrong: the chunk pin must fail."""
+    good = ecc_oracle._chunk_voxel_planes
+    if name == "lower collar plane dropped":
+        bad = lambda n0, lo, hi, c: (lo, good(n0, lo, hi, c)[1]) if c == "V" \
+            else good(n0, lo, hi, c)  # noqa: E731
+        conv = "V"
+    else:
+        bad = lambda n0, lo, hi, c: (lo, min(hi, n0)) if c == "T" \
+            else good(n0, lo, hi, c)  # noqa: E731
+        conv = "T"
+    monkeypatch.setattr(ecc_oracle, "_chunk_voxel_planes", bad)
+    with pytest.raises((AssertionError, ValueError, IndexError)):
+        _float_chunk_pin(conv, (6, 5, 7), 17)
+
+
 def test_float_negative_zero_is_zero():
     img = np.array([[0.0, -0.0], [1.0, -0.0]], dtype=np.float32)
     t, chi = oracle.ecc_pairs_float(img, "V")

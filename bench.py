@@ -1,6 +1,6 @@
-"""Benchmark: Euler characteristic curve of a 512^3 uint8 image on one GB300.
+"""Benchmark: Euler characteristic curves on one GB300, every configured workload.
 
-Workload (one "step"): the whole hot path -- per-voxel change of Algorithm 1
+Headline (one "step"): the whole hot path -- per-voxel change of Algorithm 1
 (contribution kernel, block-private histogram, int64 merge) and the prefix
 scan -- on a 512 x 512 x 512 uint8 image (seeded white noise, Gaussian
 sigma = 4, requantised to 0..255; 256 thresholds), resident in HBM.
@@ -10,13 +10,20 @@ sigma = 4, requantised to 0..255; 256 thresholds), resident in HBM.
              the timed events.
   e2e        same metric through ecc_compute() with the image in pinned host
              memory: host->device copy, kernels, device->host curve, all timed.
-  roofline   contribution kernel: algorithmic bytes (1 byte per voxel read
-             once + 8 bytes per bin written) / its event-timed duration,
-             against the measured HBM copy bandwidth.
+  roofline   contribution kernel, integer-logic bound (see alu_ops_per_voxel),
+             with the HBM view (algorithmic bytes over its duration against
+             the measured copy bandwidth) beside it.
   cpu_baseline  the CPU oracle on a bounded slab of the same image.
 
+The same line carries the other workloads, each with its own value, roofline,
+e2e and CPU baseline: ``configs`` holds the 2D 512^2 uint8 call, the 14-bit
+3072 x 3072 x 1536 volume (resident, and streamed in z-slabs from pinned host
+memory) and the 4D 128^4 float32 field (exact pairs); ``batched`` and
+``serving`` the 4096-request mixed stream; ``h2d_peak`` the host-to-device
+copy rate the streamed and end-to-end fractions are taken against.
+
 N > 1 (torchrun): replicas, one image per rank, weak scaling; value is the
-voxels of all ranks / the slowest rank's time.
+voxels of all ranks / the slowest rank's time (headline only).
 """
 from __future__ import annotations
 
@@ -163,15 +170,19 @@ def measured_peak_hbm():
 
 
 def _oracle_planes(task):
-    """Worker of the CPU baseline: the oracle's VCEC of the cells whose axis-0
-    coordinate lies in [lo, hi), reading the image from shared memory."""
+    """Worker of the CPU baselines: the oracle's VCEC (integer image) or
+    value-keyed map (float image) of the cells whose axis-0 coordinate lies
+    in [lo, hi), reading the image from shared memory."""
     name, shape, dtype, bins, lo, hi = task
     from multiprocessing import shared_memory
     import oracle
     shm = shared_memory.SharedMemory(name=name)
     try:
         img = np.ndarray(shape, dtype=dtype, buffer=shm.buf)
-        oracle.vcec_int_zrange(img, bins, lo, hi, "V")
+        if img.dtype.kind == "f":
+            oracle.vcec_float_zrange(img, lo, hi, "V")
+        else:
+            oracle.vcec_int_zrange(img, bins, lo, hi, "V")
     finally:
         shm.close()
     return hi - lo
@@ -188,7 +199,10 @@ def oracle_on_host_cores(img, bins: int, seconds: float):
     import oracle
     procs = max(1, os.cpu_count() or 1)
     t0 = time.perf_counter()
-    oracle.vcec_int_zrange(img, bins, 0, 1, "V")
+    if img.dtype.kind == "f":
+        oracle.vcec_float_zrange(img, 0, 1, "V")
+    else:
+        oracle.vcec_int_zrange(img, bins, 0, 1, "V")
     one = max(time.perf_counter() - t0, 1e-3)
     # planes per task so that one round of tasks (one per process) takes
     # about `seconds`, at most the whole image split over the processes
@@ -207,17 +221,91 @@ def oracle_on_host_cores(img, bins: int, seconds: float):
     finally:
         shm.close()
         shm.unlink()
-    return planes * img.shape[1] * img.shape[2], wall, procs, k, rounds
+    return planes * int(np.prod(img.shape[1:])), wall, procs, k, rounds
 
 
-def cpu_baseline(img, seconds: float = 15.0):
+def cpu_baseline(img, bins: int = BINS, seconds: float = 15.0, what: str = "the same 512^3 image"):
     """The oracle on a bounded sample of the same image, on all host cores."""
-    vox, wall, procs, k, rounds = oracle_on_host_cores(img, BINS, seconds)
+    vox, wall, procs, k, rounds = oracle_on_host_cores(img, bins, seconds)
     return {"value": vox / wall / 1e9, "unit": "Gvoxel/s", "cores": procs, "kind": "oracle",
             "sample": f"{rounds} rounds of {procs} processes x cells of {k} consecutive planes "
-                      f"of the same 512^3 image: {vox} voxels in {wall:.1f} s "
+                      f"of {what}: {vox} voxels in {wall:.1f} s "
                       f"(~{wall * procs:.0f} s of CPU work; numpy oracle, one process per "
                       "host core)"}
+
+
+def _numa_info(ptr: int):
+    """NUMA node of the page at host address ptr, the GPU's node and the
+    number of nodes (None where the system does not say)."""
+    import ctypes
+    info = {"buffer_node": None, "gpu_node": None, "nodes": None}
+    try:
+        info["nodes"] = len([n for n in os.listdir("/sys/devices/system/node")
+                             if n.startswith("node") and n[4:].isdigit()])
+    except OSError:
+        pass
+    try:
+        libc = ctypes.CDLL(None, use_errno=True)
+        nr = {"aarch64": 236, "x86_64": 239}.get(os.uname().machine)
+        node = ctypes.c_int(-1)
+        if nr is not None and libc.syscall(nr, ctypes.byref(node), None, ctypes.c_ulong(0),
+                                           ctypes.c_void_p(ptr), ctypes.c_ulong(3)) == 0:
+            info["buffer_node"] = node.value
+    except Exception:
+        pass
+    try:
+        bus = subprocess.run(["nvidia-smi", "-i", "0", "--query-gpu=pci.bus_id",
+                              "--format=csv,noheader"], capture_output=True, text=True,
+                             timeout=10).stdout.strip().lower()
+        if bus:
+            path = f"/sys/bus/pci/devices/{bus[-12:]}/numa_node"
+            info["gpu_node"] = int(open(path).read().strip())
+    except Exception:
+        pass
+    return info
+
+
+def h2d_peak():
+    """Pinned host -> device copy rate: one 4 GiB pinned buffer copied whole by
+    one stream, and in equal parts by 2 and 4 concurrent streams (best of 3
+    each), with the NUMA placement of the buffer and of the GPU."""
+    import torch
+    size = 4 << 30
+    host = torch.empty(size, dtype=torch.uint8, pin_memory=True)
+    host.fill_(1)
+    dev = torch.empty(size, dtype=torch.uint8, device="cuda")
+    rates = {}
+    for ns in (1, 2, 4):
+        streams = [torch.cuda.Stream() for _ in range(ns)]
+        part = size // ns
+        best = 0.0
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for i, st in enumerate(streams):
+                with torch.cuda.stream(st):
+                    dev[i * part:(i + 1) * part].copy_(host[i * part:(i + 1) * part],
+                                                       non_blocking=True)
+            torch.cuda.synchronize()
+            best = max(best, size / (time.perf_counter() - t0) / 1e9)
+        rates[str(ns)] = best
+    info = _numa_info(host.data_ptr())
+    del host, dev
+    torch.cuda.empty_cache()
+    return {"gbs": max(rates.values()), "by_streams": rates, "buffer_bytes": size, **info}
+
+
+def alu_roofline(nvox: int, ops_per_voxel: float, kernel_s: float, alu_pk: float,
+                 hbm_bytes: float, hbm_pk: float, hbm_kind: str, what: str):
+    """Roofline object of an integer-logic bound kernel, with the HBM view of
+    its algorithmic bytes beside it."""
+    achieved = nvox * ops_per_voxel / kernel_s / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": alu_pk, "unit": "Tops/s",
+            "frac": achieved / alu_pk, "traffic": None, "kernel": what,
+            "kernel_ms": kernel_s * 1e3, "ops_per_voxel": ops_per_voxel,
+            "peak_kind": "derived: SMs x 64 logic lanes/clock x max SM clock",
+            "hbm": {"achieved": hbm_bytes / kernel_s / 1e9, "peak": hbm_pk, "unit": "GB/s",
+                    "frac": hbm_bytes / kernel_s / 1e9 / hbm_pk, "peak_kind": hbm_kind}}
 
 
 def make_requests(n: int, seed: int):
@@ -313,14 +401,16 @@ def bench_serving(h, reqs, rate_hz: float, seed: int, borrowed: bool = False):
             "gvox_s": vox / wall / 1e9, "wall_s": wall}
 
 
-def workload_stream(args):
+def config_volume14(steps: int, volume, h2d: dict):
     """14-bit two-phase volume (default 1536 x 3072 x 3072 uint16, 27 GiB,
-    16384 bins): streamed from pinned host memory in z-slabs of 64 planes
-    through a 4 GiB device ring, and fully resident, same bytes; the
-    pinned host->device copy peak measured beside them."""
+    16384 bins), the same bytes fully resident in HBM (value: events around
+    ecc_compute_device on the device image) and streamed from pinned host
+    memory in z-slabs of 64 planes through a 4 GiB device ring (e2e: the
+    wall time of begin / push every slab / finish, min and median over the
+    repetitions)."""
     import torch
     from paper_1705_02045_gb300 import ecc, synth
-    shape = tuple(int(s) for s in args.volume.split(","))
+    shape = tuple(int(s) for s in volume)
     nvox = int(np.prod(shape))
     host = torch.empty(shape, dtype=torch.int16, pin_memory=True)
     hview = host.numpy().view(np.uint16)
@@ -329,27 +419,10 @@ def workload_stream(args):
         hview[z0:z0 + slab.shape[0]] = slab
     gen_s = time.perf_counter() - t0
     hu = host.view(torch.uint16)
-    # pinned H2D copy rate: the first 4 GiB (best of 3), then every 4 GiB
-    # chunk of the whole volume once (the same host pages the stream reads)
-    flat = host.reshape(-1)
-    step = (4 << 30) // 2
-    dbuf = torch.empty(step, dtype=torch.int16, device="cuda")
-
-    def h2d_once(lo):
-        n = min(step, flat.numel() - lo)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        dbuf[:n].copy_(flat[lo:lo + n], non_blocking=True)
-        torch.cuda.synchronize()
-        return n * 2 / (time.perf_counter() - t0) / 1e9
-
-    h2d_gbs = max(h2d_once(0) for _ in range(3))
-    chunk_gbs = [h2d_once(lo) for lo in range(0, flat.numel(), step)]
-    del dbuf
     # streamed
     h = ecc.ecc_create(device=0, bins=16384, slab_depth=64, ring_bytes=4 << 30)
     times, curve_s = [], None
-    for rep in range(args.steps + 1):
+    for rep in range(steps + 1):
         t0 = time.perf_counter()
         s = ecc.ecc_stream_begin(h, shape, np.uint16)
         for z0 in range(0, shape[0], 64):
@@ -357,7 +430,6 @@ def workload_stream(args):
         curve_s = ecc.ecc_stream_finish(h, s)
         if rep:
             times.append(time.perf_counter() - t0)
-    t_stream = min(times)
     ecc.ecc_destroy(h)
     # resident
     d = hu.cuda()
@@ -369,44 +441,50 @@ def workload_stream(args):
     st.synchronize()
     ecc.ecc_set_profiling(h, True)
     ecc.ecc_profile_read(h)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    ev[0].record(st)
-    for _ in range(args.steps):
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    for e0, e1 in evs:
+        e0.record(st)
         ecc.ecc_compute_device(h, d, 16384, c, stream=st)
-    ev[1].record(st)
+        e1.record(st)
     st.synchronize()
-    t_res = ev[0].elapsed_time(ev[1]) / 1e3 / args.steps
+    t_res = float(np.median([e0.elapsed_time(e1) for e0, e1 in evs])) / 1e3
     kms, n = ecc.ecc_profile_read(h)
     assert ecc.ecc_device_status(h) == ecc.ECC_OK
     curve_r = c.cpu().numpy()
     ecc.ecc_destroy(h)
+    del d
+    torch.cuda.empty_cache()
     same = bool(np.array_equal(curve_s, curve_r))
     assert same and curve_r[-1] == 1
     peak, peak_kind = measured_peak_hbm()
     kernel_s = kms / max(n, 1) / 1e3
     alu_pk = alu_peak_tops(torch.cuda.get_device_properties(0).multi_processor_count, None)
-    print(json.dumps({
-        "metric": METRIC, "workload": "stream", "value": nvox / t_stream / 1e9,
-        "unit": "Gvoxel/s", "n_gpus": 1, "steps": args.steps, "dtype": "u16",
-        "data": "synthetic",
-        "config": {"workload": f"3D {shape} uint16 14-bit two-phase field sigma=6, 16384 bins; "
-                               "z-slabs of 64 planes, 4 GiB ring, pinned host memory"},
-        "streamed": {"seconds": t_stream, "gvox_s": nvox / t_stream / 1e9,
-                     "h2d_gbs": nvox * 2 / t_stream / 1e9,
-                     "fraction_of_h2d_peak": (nvox * 2 / t_stream / 1e9) / h2d_gbs},
-        "resident": {"seconds": t_res, "gvox_s": nvox / t_res / 1e9,
-                     "kernel_s": kernel_s,
-                     "roofline": {"bound": "alu",
-                                  "achieved": nvox * alu_ops_per_voxel(14) / kernel_s / 1e12,
-                                  "peak": alu_pk, "unit": "Tops/s",
-                                  "frac": nvox * alu_ops_per_voxel(14) / kernel_s / 1e12 / alu_pk,
-                                  "ops_per_voxel": alu_ops_per_voxel(14),
-                                  "hbm": {"achieved": nvox * 2 / kernel_s / 1e9, "peak": peak,
-                                          "unit": "GB/s",
-                                          "frac": nvox * 2 / kernel_s / 1e9 / peak}}},
-        "h2d_peak_gbs": h2d_gbs, "h2d_chunk_gbs": [round(x, 1) for x in chunk_gbs],
-        "streamed_rep_seconds": times, "streamed_equals_resident": same,
-        "generation_s": gen_s}), flush=True)
+    t_min, t_med = min(times), float(np.median(times))
+    base = cpu_baseline(np.ascontiguousarray(hview[:32]), 16384, 10.0,
+                        f"the first 32 planes of the same {shape[1]}x{shape[2]} volume")
+    del host, hview, hu
+    return {
+        "workload": f"3D {shape[2]}x{shape[1]}x{shape[0]} uint16 14-bit two-phase field "
+                    "sigma=6 (Gaussian random field at its 40th percentile, phases "
+                    "N(3000,400) / N(11000,900)), 16384 bins",
+        "value": nvox / t_res / 1e9, "unit": "Gvoxel/s", "ms_per_step": t_res * 1e3,
+        "steps": steps, "dtype": "u16",
+        "timing": "resident: median of CUDA events around ecc_compute_device on the device "
+                  "image (input 27 GiB > L2)",
+        "roofline": alu_roofline(nvox, alu_ops_per_voxel(14), kernel_s, alu_pk, nvox * 2.0,
+                                 peak, peak_kind, "bit-sliced contribution+histogram"),
+        "e2e": {"value": nvox / t_min / 1e9, "unit": "Gvoxel/s",
+                "median": nvox / t_med / 1e9,
+                "h2d_bytes_per_step": nvox * 2, "d2h_bytes_per_step": 16384 * 8,
+                "how": "ecc_stream_begin / ecc_stream_push_slab of 64-plane slabs from pinned "
+                       "host memory / ecc_stream_finish (4 GiB device ring), wall clock, best "
+                       f"of {steps}",
+                "h2d_gbs": nvox * 2 / t_min / 1e9,
+                "frac_of_h2d_peak": nvox * 2 / t_min / 1e9 / h2d["gbs"],
+                "rep_seconds": times},
+        "cpu_baseline": base,
+        "streamed_equals_resident": same, "generation_s": gen_s}
 
 
 def workload_f32q(args):
@@ -508,7 +586,7 @@ def workload_file(args):
         shutil.rmtree(tmpdir, ignore_errors=True)
 
 
-def workload_plane(args):
+def config_plane512(steps: int, warmup: int):
     """2D 512 x 512 uint8, i.i.d. uniform 0..255, 256 bins: one small image
     per call, bound by launch latency. Device time of each call (events
     around it, L2 flushed between calls outside the events), the same call
@@ -523,7 +601,7 @@ def workload_plane(args):
     h = ecc.ecc_create(device=0)
     st = torch.cuda.Stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    for _ in range(max(args.warmup, 3)):
+    for _ in range(max(warmup, 3)):
         ecc.ecc_compute_device(h, d, 256, c, stream=st)
     st.synchronize()
     ref = c.cpu().numpy().copy()
@@ -531,7 +609,7 @@ def workload_plane(args):
 
     def timed(run):
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
+               for _ in range(steps)]
         for a, b in evs:
             with torch.cuda.stream(st):
                 flush.zero_()
@@ -542,8 +620,12 @@ def workload_plane(args):
         return float(np.median([a.elapsed_time(b) for a, b in evs]))
 
     launches0 = ecc.ecc_launch_count(h)
+    ecc.ecc_set_profiling(h, True)
+    ecc.ecc_profile_read(h)
     direct_ms = timed(lambda: ecc.ecc_compute_device(h, d, 256, c, stream=st))
-    launches = (ecc.ecc_launch_count(h) - launches0) // args.steps
+    kms, n = ecc.ecc_profile_read(h)
+    ecc.ecc_set_profiling(h, False)
+    launches = (ecc.ecc_launch_count(h) - launches0) // steps
     c.zero_()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=st):
@@ -554,54 +636,91 @@ def workload_plane(args):
     for _ in range(3):
         ecc.ecc_compute(h, hp)
     e2e = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         t0 = time.perf_counter()
         curve = ecc.ecc_compute(h, hp)
         e2e.append(time.perf_counter() - t0)
     assert np.array_equal(curve, ref)
     ecc.ecc_destroy(h)
     e2e_s = float(np.median(e2e))
-    print(json.dumps({
-        "metric": METRIC, "workload": "plane512", "value": nvox / (direct_ms * 1e-3) / 1e9,
-        "unit": "Gvoxel/s", "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3),
-        "ms_per_step": direct_ms, "higher_is_better": True, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": "2D 512x512 uint8 i.i.d. uniform 0..255, 256 bins, one image "
-                               "per call, device-resident",
-                   "l2": "256 MiB write between calls, outside the timed events"},
+    kernel_s = kms / max(n, 1) / 1e3
+    peak, peak_kind = measured_peak_hbm()
+    alg = nvox + 256 * 8
+    return {
+        "workload": "2D 512x512 uint8 i.i.d. uniform 0..255, 256 bins, one image per call, "
+                    "device-resident",
+        "value": nvox / (direct_ms * 1e-3) / 1e9, "unit": "Gvoxel/s",
+        "ms_per_step": direct_ms, "steps": steps, "dtype": "u8",
+        "timing": "median of CUDA events around each ecc_compute_device call; 256 MiB write "
+                  "between calls, outside the events",
         "us_per_call": direct_ms * 1e3, "graph_us_per_call": graph_ms * 1e3,
         "graph_gvox_s": nvox / (graph_ms * 1e-3) / 1e9, "launches_per_call": int(launches),
+        "roofline": {"bound": "hbm", "achieved": alg / kernel_s / 1e9, "peak": peak,
+                     "unit": "GB/s", "frac": alg / kernel_s / 1e9 / peak, "traffic": None,
+                     "kernel": "bit-sliced contribution+histogram+fused scan",
+                     "kernel_ms": kernel_s * 1e3, "peak_kind": peak_kind,
+                     "note": "launch-latency bound: 256 KiB read by one launch of a few "
+                             "microseconds"},
         "e2e": {"value": nvox / e2e_s / 1e9, "unit": "Gvoxel/s", "us_per_call": e2e_s * 1e6,
-                "h2d_bytes_per_step": nvox, "d2h_bytes_per_step": 256 * 8}}), flush=True)
+                "h2d_bytes_per_step": nvox, "d2h_bytes_per_step": 256 * 8},
+        "cpu_baseline": cpu_baseline(img, 256, 3.0, "the same 512^2 image")}
 
 
-def workload_f32(args):
-    """4D 128^4 float32 Gaussian random field (sigma = 3 per axis): pairs,
-    radix sort, reduce-by-key and scan, device-resident input."""
+def config_grf4d(steps: int, volume):
+    """4D 128^4 float32 Gaussian random field (sigma = 3 per axis): (key,
+    change) pairs, radix sort, reduce-by-key and scan into exact (threshold,
+    chi) pairs. value: the blocking ecc_compute on the device-resident image
+    (pairs copied to the host), median over the steps; e2e: the same from
+    pinned host memory."""
     import torch
     from paper_1705_02045_gb300 import ecc, synth
-    shape = tuple(int(s) for s in args.volume.split(","))
+    shape = tuple(int(s) for s in volume)
     nvox = int(np.prod(shape))
     d = synth.grf_f32_torch(shape, 3.0, synth.SEED_BASE + 4).contiguous()
     torch.cuda.synchronize()
     h = ecc.ecc_create(device=0)
     t, chi = ecc.ecc_compute(h, d)
+    ecc.ecc_set_profiling(h, True)
+    ecc.ecc_profile_read(h)
     times = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         t, chi = ecc.ecc_compute(h, d)
         times.append(time.perf_counter() - t0)
+    kms, n = ecc.ecc_profile_read(h)
+    ecc.ecc_set_profiling(h, False)
+    hp = d.cpu().pin_memory()
+    ecc.ecc_compute(h, hp)
+    e2e = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        t2, chi2 = ecc.ecc_compute(h, hp)
+        e2e.append(time.perf_counter() - t0)
     ecc.ecc_destroy(h)
     assert chi[-1] == 1 and np.all(np.diff(t) > 0)
-    best = min(times)
-    print(json.dumps({
-        "metric": METRIC, "workload": "f32_4d", "value": nvox / best / 1e9,
-        "unit": "Gvoxel/s", "n_gpus": 1, "steps": args.steps, "dtype": "f32",
-        "data": "synthetic",
-        "config": {"workload": f"4D {shape} float32 Gaussian random field sigma=3, "
-                               "device-resident, exact (threshold, chi) pairs"},
-        "seconds": best, "pairs": int(len(t)),
-        "ms_per_step": best * 1e3}), flush=True)
+    assert np.array_equal(t, t2) and np.array_equal(chi, chi2)
+    med, e2e_med = float(np.median(times)), float(np.median(e2e))
+    kernel_s = kms / max(n, 1) / 1e3
+    peak, peak_kind = measured_peak_hbm()
+    alu_pk = alu_peak_tops(torch.cuda.get_device_properties(0).multi_processor_count, None)
+    base = cpu_baseline(hp[:16].numpy().copy(), 0, 10.0,
+                        f"the first 16 volumes of the same {shape} field")
+    del d, hp
+    torch.cuda.empty_cache()
+    return {
+        "workload": f"4D {'x'.join(map(str, shape))} float32 Gaussian random field sigma=3, "
+                    "exact (threshold, chi) pairs, device-resident",
+        "value": nvox / med / 1e9, "unit": "Gvoxel/s", "ms_per_step": med * 1e3,
+        "steps": steps, "dtype": "f32", "pairs": int(len(t)),
+        "timing": "median wall time of the blocking ecc_compute on the device image "
+                  "(contribution kernel, radix sort, reduce-by-key, scan, pairs to the host); "
+                  "input 1 GiB > L2",
+        "roofline": alu_roofline(nvox, 40.0, kernel_s, alu_pk, nvox * 4.0, peak, peak_kind,
+                                 "4D contribution kernel emitting (key, change) pairs"),
+        "e2e": {"value": nvox / e2e_med / 1e9, "unit": "Gvoxel/s",
+                "h2d_bytes_per_step": nvox * 4, "d2h_bytes_per_step": int(len(t)) * 12},
+        "cpu_baseline": base}
 
 
 def profile_case(args):
@@ -687,35 +806,44 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--batch-images", type=int, default=1024,
+    ap.add_argument("--batch-images", type=int, default=4096,
                     help="images of the mixed request stream in the batched comparison")
     ap.add_argument("--serve-requests", type=int, default=4096,
                     help="requests of the served Poisson stream (0 = skip)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="headline only: skip the 2D, 14-bit volume and 4D float workloads")
+    ap.add_argument("--config-steps", type=int, default=5,
+                    help="repetitions of each workload in configs")
     ap.add_argument("--profile-launches", type=int, default=0,
                     help="only run this many ecc_compute_device launches (for ncu) and exit")
     ap.add_argument("--profile-shape", default="640,512,512")
     ap.add_argument("--profile-dtype", default="u8", choices=["u8", "u16"])
     ap.add_argument("--workload", default="resident512",
                     choices=["resident512", "stream", "f32_4d", "plane512", "f32q", "file"],
-                    help="resident512: the headline line; the others print one line each: "
-                         "stream (14-bit volume from pinned memory), file (the same recipe "
-                         "from a raw file), f32_4d (exact float pairs), f32q (value "
-                         "transform), plane512 (2D 512^2)")
+                    help="resident512: the full line (headline and every workload); the "
+                         "others print one line each: stream (14-bit volume resident and from "
+                         "pinned memory), file (the same recipe from a raw file), f32_4d "
+                         "(exact float pairs), f32q (value transform), plane512 (2D 512^2)")
     ap.add_argument("--volume", default=None, help="shape for --workload stream / f32_4d")
     args = ap.parse_args()
     world, rank, local = _dist()
     if args.profile_launches > 0:
         profile_case(args)
         return
-    if args.workload == "plane512":
-        workload_plane(args)
+    if args.workload in ("plane512", "stream", "f32_4d"):
+        if args.workload == "plane512":
+            res = config_plane512(args.steps, args.warmup)
+        elif args.workload == "stream":
+            res = config_volume14(max(1, min(args.steps, 5)),
+                                  (args.volume or "1536,3072,3072").split(","), h2d_peak())
+        else:
+            res = config_grf4d(max(1, min(args.steps, 20)),
+                               (args.volume or "128,128,128,128").split(","))
+        print(json.dumps({"metric": METRIC, "workload_key": args.workload, "n_gpus": 1,
+                          "higher_is_better": True, "data": "synthetic", **res}), flush=True)
         return
     if args.workload != "resident512":
         args.steps = max(1, min(args.steps, 5))
-    if args.workload == "stream":
-        args.volume = args.volume or "1536,3072,3072"
-        workload_stream(args)
-        return
     if args.workload == "file":
         args.volume = args.volume or "256,3072,3072"
         workload_file(args)
@@ -723,10 +851,6 @@ def main():
     if args.workload == "f32q":
         args.volume = args.volume or "128,128,128,128"
         workload_f32q(args)
-        return
-    if args.workload == "f32_4d":
-        args.volume = args.volume or "128,128,128,128"
-        workload_f32(args)
         return
     if args.impl == "reference":
         run_reference(args, world, rank)
@@ -876,6 +1000,21 @@ def main():
                                                 "the same handle")
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(img)
+        if not args.no_configs:
+            # the other configured workloads, each with its own value, roofline,
+            # e2e and CPU baseline (the oracle on a bounded sample)
+            del d_img, flush
+            torch.cuda.empty_cache()
+            line["h2d_peak"] = h2d_peak()
+            cs = args.config_steps
+            line["configs"] = {
+                "plane512_u8": config_plane512(max(cs, 20), args.warmup),
+                "volume14_u16": config_volume14(max(1, min(cs, 5)), (1536, 3072, 3072),
+                                                line["h2d_peak"]),
+                "grf4d_f32": config_grf4d(max(1, cs), (128, 128, 128, 128)),
+            }
+            # one byte per voxel crosses the host link
+            line["e2e"]["frac_of_h2d_peak"] = e2e_value / world / line["h2d_peak"]["gbs"]
         print(json.dumps(line), flush=True)
     ecc.ecc_destroy(h)
     if world > 1:

@@ -252,8 +252,8 @@ int ecc_request_latency_us(ecc_handle* h, uint64_t req_id, double* us);
 int64_t ecc_launch_count(const ecc_handle* h);
 
 /* Instrumentation (no counterpart in the paper). With profiling on, every
- * integer computation records CUDA events on its launching stream around its
- * contribution kernel(s). ecc_profile_read synchronises, returns the summed
+ * single-image computation (integer curve or float pairs) records CUDA events
+ * on its launching stream around its contribution kernel(s). ecc_profile_read synchronises, returns the summed
  * elapsed milliseconds and the number of computations recorded since the
  * last read, and clears the record. */
 int ecc_set_profiling(ecc_handle* h, int on);

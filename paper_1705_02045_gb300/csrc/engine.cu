@@ -347,8 +347,23 @@ static int compute_float(ecc_handle* h, const void* d_img, const Shape& s, ecc_r
   a.pair_count = h->pair_count.as<unsigned long long>();
   a.pair_cap = n;
   a.stream = st;
+  cudaEvent_t pa = nullptr, pb = nullptr;  // profiling: events around the pairs kernel
+  if (h->prof_on) {
+    if ((e = cudaEventCreate(&pa)) || (e = cudaEventCreate(&pb)) || (e = cudaEventRecord(pa, st))) {
+      if (pa) cudaEventDestroy(pa);
+      if (pb) cudaEventDestroy(pb);
+      return cuda_err(h, e, "profiling event");
+    }
+  }
   int64_t cnt = 0;
-  if ((e = launch_local(a, h->num_sms, &cnt))) return cuda_err(h, e, "pairs kernel");
+  e = launch_local(a, h->num_sms, &cnt);
+  if (pa && e == cudaSuccess && (e = cudaEventRecord(pb, st)) == cudaSuccess) {
+    h->prof_events.emplace_back(pa, pb);
+  } else if (pa) {
+    cudaEventDestroy(pa);
+    cudaEventDestroy(pb);
+  }
+  if (e) return cuda_err(h, e, "pairs kernel");
   h->launches += cnt;
   unsigned long long npairs = 0;
   if ((e = cudaMemcpyAsync(&npairs, h->pair_count.p, 8, cudaMemcpyDeviceToHost, st)))

@@ -45,6 +45,7 @@ struct LocalArgs {
   int variant = 0;              // kernel variant (0 = generic key kernel)
   int zc = 0;                   // planes per tile along the marching axis (0 = auto)
   int warps = 0;                // bit-sliced kernel: warps per block (0 = auto)
+  int layout = 0;               // bit-sliced kernel: 0 auto, 1 row groups, 2 warp columns
   int hist = 0;                 // bit-sliced kernel histogram: 0 auto (shared memory when
                                 // bins <= kSmemBinsMax), 1 shared memory, 2 global atomics
   long long* fused_curve = nullptr;  // bit-sliced kernel: the last block to finish writes

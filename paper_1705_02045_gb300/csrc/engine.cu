@@ -178,6 +178,7 @@ int enqueue_int(ecc_handle* h, const void* d_img, int64_t row_pitch, const Shape
     a.variant = h->variant;
     a.warps = h->bits_warps;
     a.zc = h->bits_zc;
+    a.layout = h->bits_layout;
     a.vcec = d_vcec;
     a.err = h->errw.as<int>();
     a.stream = stream;
@@ -186,7 +187,7 @@ int enqueue_int(ecc_handle* h, const void* d_img, int64_t row_pitch, const Shape
     const int64_t step = max_planes_per_launch(s, h->num_sms);
     // launch shape from the tuner (first image of a shape class tunes it)
     if (h->tuner && a.view == 3 && bits_nb(dtype, bins) && h->variant != 1 &&
-        h->bits_warps == 0 && h->bits_zc == 0) {
+        h->bits_warps == 0 && h->bits_zc == 0 && h->bits_layout == 0) {
       LocalArgs t = a;
       t.w_lo = 0;
       t.w_hi = std::min(a.n[0], step);
@@ -205,6 +206,7 @@ int enqueue_int(ecc_handle* h, const void* d_img, int64_t row_pitch, const Shape
       a.warps = c.warps;
       a.zc = c.zc;
       a.hist = c.hist;
+      a.layout = c.layout;
     }
     // one bit-sliced launch over the whole image: its last block also writes
     // the curve and leaves VCEC and the block counter at zero, so neither the
@@ -447,6 +449,10 @@ int ecc_create(const ecc_config* cfg, ecc_handle** out) {
   }
   // launch-shape overrides for tuning sweeps of the bit-sliced kernel
   if (const char* w = std::getenv("ECC_BITS_WARPS")) h->bits_warps = std::atoi(w);
+  if (const char* l = std::getenv("ECC_BITS_LAYOUT")) {
+    if (!std::strcmp(l, "rows")) h->bits_layout = 1;
+    else if (!std::strcmp(l, "columns")) h->bits_layout = 2;
+  }
   if (const char* z = std::getenv("ECC_BITS_ZC")) h->bits_zc = std::atoi(z);
   if (h->cfg.tuner_cache || std::getenv("ECC_TUNE")) {
     h->tuner = new (std::nothrow) Tuner();

@@ -58,7 +58,8 @@ struct TuneChoice {
   int warps = 0;
   int zc = 0;
   float ms = 0.f;
-  int hist = 0;  // LocalArgs::hist
+  int hist = 0;    // LocalArgs::hist
+  int layout = 0;  // LocalArgs::layout (0: the default for the value bits)
 };
 
 struct Tuner {
@@ -80,6 +81,7 @@ struct ecc_handle {
   int variant = 0;                     // contribution kernel: 0 auto, 1 generic, 2 bit-sliced
   int bits_warps = 0;                  // bit-sliced kernel warps per block (0 = auto)
   int bits_zc = 0;                     // bit-sliced kernel planes per tile (0 = auto)
+  int bits_layout = 0;                 // bit-sliced kernel: 0 auto, 1 row groups, 2 warp columns
   ecc::Tuner* tuner = nullptr;         // launch-shape tuner (tuner_cache set or ECC_TUNE)
   cudaStream_t stream = nullptr;       // compute
   cudaStream_t copy_stream = nullptr;  // host <-> device

@@ -2,11 +2,12 @@
 //
 // For each shape class (value bits, lanes per row group, convention, and the
 // base-2 logarithms of the row count and of the plane count) the first image
-// of the class times a few launch shapes -- warps per block (rows per block)
-// and planes per tile (or equal plane spans per block), then block-private
-// shared-memory histograms against
-// direct global atomics for the fastest shape -- on its own data, keeps the
-// fastest, and reuses it for every later image of the class. With
+// of the class times a few launch shapes -- the row-group layout with warps
+// per block (rows per block) and planes per tile (or equal plane spans per
+// block), the warp-column layout with warps per block, then block-private
+// shared-memory histograms against direct global atomics for the fastest
+// shape -- on its own data, keeps the fastest, and reuses it for every later
+// image of the class. With
 // ecc_config.tuner_cache set, the table is read from and appended to that
 // file (one JSON object per line).
 #include "engine.h"
@@ -52,12 +53,13 @@ void Tuner::load(const std::string& file) {
   char line[256];
   while (std::fgets(line, sizeof line, f)) {
     char k[96] = {0};
-    int w = 0, z = 0, hm = 0;
+    int w = 0, z = 0, hm = 0, lay = 0;
     float ms = 0;
-    const int got =
-        std::sscanf(line, " {\"key\": \"%95[^\"]\", \"warps\": %d, \"zc\": %d, \"ms\": %f, \"hist\": %d",
-                    k, &w, &z, &ms, &hm);
-    if (got >= 4 && w > 0 && z >= 0) table[k] = TuneChoice{w, z, ms, got == 5 ? hm : 0};
+    const int got = std::sscanf(
+        line, " {\"key\": \"%95[^\"]\", \"warps\": %d, \"zc\": %d, \"ms\": %f, \"hist\": %d, \"layout\": %d",
+        k, &w, &z, &ms, &hm, &lay);
+    if (got >= 4 && w > 0 && z >= 0)
+      table[k] = TuneChoice{w, z, ms, got >= 5 ? hm : 0, got >= 6 ? lay : 0};
   }
   std::fclose(f);
 }
@@ -75,8 +77,10 @@ void Tuner::store(const std::string& k, const TuneChoice& c) {
   table[k] = c;
   if (path.empty()) return;
   if (FILE* f = std::fopen(path.c_str(), "a")) {
-    std::fprintf(f, "{\"key\": \"%s\", \"warps\": %d, \"zc\": %d, \"ms\": %.6f, \"hist\": %d}\n",
-                 k.c_str(), c.warps, c.zc, c.ms, c.hist);
+    std::fprintf(f,
+                 "{\"key\": \"%s\", \"warps\": %d, \"zc\": %d, \"ms\": %.6f, \"hist\": %d, "
+                 "\"layout\": %d}\n",
+                 k.c_str(), c.warps, c.zc, c.ms, c.hist, c.layout);
     std::fclose(f);
   }
 }
@@ -109,28 +113,44 @@ int tune_bits(ecc_handle* h, const LocalArgs& base, TuneChoice* best) {
     if ((e = cudaEventElapsedTime(ms, e0, e1))) return cuda_err(h, e, "tuner timing");
     return ECC_OK;
   };
+  // row groups: warps per block x planes per tile
   for (int W : {4, 8, 16}) {
     if (W * R < 3 || W * R > 512) continue;
     for (int zc : {0, 16, 32, 64, 128}) {  // 0: balanced spans
       if (zc > 2 * planes && zc != 16) continue;
       LocalArgs a = base;
+      a.layout = 1;
       a.warps = W;
       a.zc = zc;
       a.hist = 0;
       float ms = 0;
       if ((rc = time_one(a, &ms))) break;
-      if (ms < best->ms) *best = TuneChoice{W, zc, ms, 0};
+      if (ms < best->ms) *best = TuneChoice{W, zc, ms, 0, 1};
     }
     if (rc) break;
+  }
+  // warp columns: warps per block
+  for (int W : {4, 8}) {
+    if (rc) break;
+    LocalArgs a = base;
+    a.layout = 2;
+    a.warps = W;
+    a.zc = 0;
+    a.hist = 0;
+    float ms = 0;
+    if ((rc = time_one(a, &ms))) break;
+    if (ms < best->ms) *best = TuneChoice{W, 0, ms, 0, 2};
   }
   // histogram privatisation for the fastest shape: shared memory or global
   if (!rc && best->warps > 0 && base.bins <= kSmemBinsMax) {
     LocalArgs a = base;
+    a.layout = best->layout;
     a.warps = best->warps;
     a.zc = best->zc;
     a.hist = 2;
     float ms = 0;
-    if (!(rc = time_one(a, &ms)) && ms < best->ms) *best = TuneChoice{best->warps, best->zc, ms, 2};
+    if (!(rc = time_one(a, &ms)) && ms < best->ms)
+      *best = TuneChoice{best->warps, best->zc, ms, 2, best->layout};
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -18,20 +18,24 @@ pytestmark = pytest.mark.gpu
 S = synth.SEED_BASE + 900
 
 
-def _handle(kernel, **kw):
-    old = os.environ.get("ECC_KERNEL")
-    os.environ["ECC_KERNEL"] = kernel
+def _handle(kernel, layout=None, **kw):
+    env = {"ECC_KERNEL": kernel}
+    if layout:
+        env["ECC_BITS_LAYOUT"] = layout
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update(env)
     try:
         return ecc.ecc_create(device=0, **kw)
     finally:
-        if old is None:
-            del os.environ["ECC_KERNEL"]
-        else:
-            os.environ["ECC_KERNEL"] = old
+        for k, v in old.items():
+            if v is None:
+                del os.environ[k]
+            else:
+                os.environ[k] = v
 
 
-def _both(img, bins, conv):
-    hb = _handle("bits", bins=bins, convention=conv)
+def _both(img, bins, conv, layout=None):
+    hb = _handle("bits", layout, bins=bins, convention=conv)
     hg = _handle("generic", bins=bins, convention=conv)
     try:
         return ecc.ecc_compute(hb, img), ecc.ecc_compute(hg, img)
@@ -63,18 +67,20 @@ def test_bits_u8_smooth(conv, shape):
     assert np.array_equal(got, oracle.ecc_int(img, 256, "V" if conv == 0 else "T"))
 
 
+@pytest.mark.parametrize("layout", ["rows", "columns"])
 @pytest.mark.parametrize("shape", [(9, 21, 40), (5, 33, 520), (3, 7, 1600), (8, 8)], ids=str)
-def test_bits_u16_14bit(shape):
+def test_bits_u16_14bit(shape, layout):
     img = synth.two_phase_u16(shape, 1.5, S + 11)
-    got, gen = _both(img, 16384, 0)
+    got, gen = _both(img, 16384, 0, layout)
     want = oracle.ecc_int(img, 16384, "V")
     assert np.array_equal(got, want) and np.array_equal(gen, want)
 
 
+@pytest.mark.parametrize("layout", ["rows", "columns"])
 @pytest.mark.parametrize("conv", [0, 1])
-def test_bits_u16_full_range(conv):
+def test_bits_u16_full_range(conv, layout):
     img = synth.uniform_int((6, 9, 24), 65536, S + 12, np.uint16)
-    got, _ = _both(img, 65536, conv)
+    got, _ = _both(img, 65536, conv, layout)
     assert np.array_equal(got, oracle.ecc_int(img, 65536, "V" if conv == 0 else "T"))
 
 
@@ -84,10 +90,11 @@ def test_bits_few_levels_ties():
     assert np.array_equal(got, oracle.ecc_int(img, 256, "V"))
 
 
-def test_bits_rejects_values_above_14_bits():
+@pytest.mark.parametrize("layout", ["rows", "columns"])
+def test_bits_rejects_values_above_14_bits(layout):
     img = synth.two_phase_u16((4, 5, 16), 1.5, S + 14)
     img[2, 3, 7] = 20000
-    h = _handle("bits", bins=16384)
+    h = _handle("bits", layout, bins=16384)
     try:
         with pytest.raises(ecc.EccError) as ei:
             ecc.ecc_compute(h, img)
@@ -188,6 +195,7 @@ def test_tuner_picks_and_caches_a_launch_shape(tmp_path):
     lines = open(path.decode()).read().strip().splitlines()
     assert len(lines) == 1 and '"warps"' in lines[0] and '"zc"' in lines[0]
     assert '"hist": 0' in lines[0] or '"hist": 2' in lines[0]
+    assert '"layout": 1' in lines[0] or '"layout": 2' in lines[0]
     assert tuned_launches > 2
     h = ecc.ecc_create(device=0, tuner_cache=path)
     try:

@@ -180,22 +180,18 @@ __device__ void bitsw_span(const BitsImg& im, int64_t tx, int64_t ty, int64_t z0
   uint32_t raw[RAW];
 #pragma unroll
   for (int i = 0; i < RAW; ++i) raw[i] = 0u;
-  uint32_t Pz[NP], Ryp[NP], Pn[NP], Pup[NP], Pdn[NP];
-  // this lane's comparison words G_(1,dy,dx) of the previous step; a tile at
-  // z0 = 0 has no plane below (outside: every neighbour there comes after, so
-  // the words are zero); otherwise one priming step at z0 - 1 computes them
-  uint32_t G0p[3] = {0u, 0u, 0u}, G1p[3] = {0u, 0u, 0u}, G2p[3] = {0u, 0u, 0u};
-  const int64_t zs = z0 == 0 ? z0 : z0 - 1;
-  load_raw(zs, raw);
-  make_planes(zs, raw, Pz);
-#pragma unroll
-  for (int k = 0; k < NP; ++k) Ryp[k] = __shfl_down_sync(FULL, Pz[k], 1);
-  load_raw(zs + 1, raw);
 
-  for (int64_t z = zs; z < z1; ++z) {
+  // One step of the z-march at plane z: Pz / Ryp hold the own row and row
+  // y + 1 at z, Gp this lane's comparison words G_(1,dy,dx) of the previous
+  // step ([dy+1][dx+1]); the step fills Pn / Pup (own row and row y + 1 at
+  // z + 1) and G1 (this step's words), which the march copies back.
+  auto step = [&](int64_t z, const uint32_t(&Pz)[NP], const uint32_t(&Ryp)[NP],
+                  uint32_t(&Pn)[NP], uint32_t(&Pup)[NP], const uint32_t(&Gp)[3][3],
+                  uint32_t(&G1)[3][3]) {
     // planes of z + 1 (loaded one step ago); load z + 2
     make_planes(z + 1, raw, Pn);
     if (z + 2 <= z1) load_raw(z + 2, raw);
+    uint32_t Pdn[NP];
     // rows y - 1 and y + 1 at z + 1 (lanes 0 and 31 get their own row: only
     // collar results depend on it)
 #pragma unroll
@@ -220,7 +216,7 @@ __device__ void bitsw_span(const BitsImg& im, int64_t tx, int64_t ty, int64_t z0
                              (up_in && z1_in) ? xo : ALL};
     // the 13 forward comparisons, indexed by the later voxel
     const uint32_t G001 = gcmp(borrow<NB>(Pz, Cl), co[2], no_z);
-    uint32_t G01[3], G1[3][3];
+    uint32_t G01[3];
     G01[0] = gcmp(borrow<NB>(Ryp, Cr), co[0], no_yp);
     G01[1] = gcmp(borrow<NB>(Ryp, Pz), co[1], no_yp);
     G01[2] = gcmp(borrow<NB>(Ryp, Cl), co[2], no_yp);
@@ -240,8 +236,8 @@ __device__ void bitsw_span(const BitsImg& im, int64_t tx, int64_t ty, int64_t z0
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       G01dn[i] = __shfl_up_sync(FULL, G01[i], 1);
-      Gdn1[i] = __shfl_up_sync(FULL, G2p[i], 1);
-      Gup1[i] = __shfl_down_sync(FULL, G0p[i], 1);
+      Gdn1[i] = __shfl_up_sync(FULL, Gp[2][i], 1);
+      Gup1[i] = __shfl_down_sync(FULL, Gp[0][i], 1);
     }
     if (__any_sync(FULL, z >= z0 && dep != 0u) && z >= z0 && dep) {
       // forward after-bits: G shifted by dx within the word
@@ -256,7 +252,7 @@ __device__ void bitsw_span(const BitsImg& im, int64_t tx, int64_t ty, int64_t z0
         a0m[dx + 1] = ~G01dn[1 - dx];
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy) ap[dy + 1][dx + 1] = sh(G1[dy + 1][dx + 1], dx);
-        am[1][dx + 1] = ~G1p[1 - dx];
+        am[1][dx + 1] = ~Gp[1][1 - dx];
         am[0][dx + 1] = ~Gdn1[1 - dx];  // neighbour (-1,-1,dx): delta (1,+1,-dx) of row y-1
         am[2][dx + 1] = ~Gup1[1 - dx];  // neighbour (-1,+1,dx): delta (1,-1,-dx) of row y+1
       }
@@ -382,17 +378,36 @@ __device__ void bitsw_span(const BitsImg& im, int64_t tx, int64_t ty, int64_t z0
         deposit(v, N - 13);
       }
     }
+  };
+
+  uint32_t PA[NP], RA[NP], PB[NP], RB[NP];
+  // a tile at z0 = 0 has no plane below (outside: every neighbour there comes
+  // after, so the previous words are zero); otherwise one priming step at
+  // z0 - 1 computes them
+  uint32_t GA[3][3], GB[3][3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      G0p[i] = G1[0][i];
-      G1p[i] = G1[1][i];
-      G2p[i] = G1[2][i];
-    }
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) GA[i][j] = 0u;
+  const int64_t zs = z0 == 0 ? z0 : z0 - 1;
+  load_raw(zs, raw);
+  make_planes(zs, raw, PA);
+#pragma unroll
+  for (int k = 0; k < NP; ++k) RA[k] = __shfl_down_sync(FULL, PA[k], 1);
+  load_raw(zs + 1, raw);
+  // (a z-march unrolled by two, the register sets trading roles instead of
+  // being copied, measured much slower: two inlined copies of the step)
+  for (int64_t z = zs; z < z1; ++z) {
+    step(z, PA, RA, PB, RB, GA, GB);
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-      Pz[k] = Pn[k];
-      Ryp[k] = Pup[k];
+      PA[k] = PB[k];
+      RA[k] = RB[k];
     }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) GA[i][j] = GB[i][j];
   }
 }
 

@@ -152,6 +152,51 @@ constexpr int64_t kUploadChunksMax = 16;
 constexpr size_t kUploadChunkBytes = size_t(32) << 20;
 constexpr size_t kUploadTailBytes = size_t(2) << 20;
 
+// Uploads a host image of `bytes` into the handle's image buffer in plane
+// chunks on the copy stream: equal chunks of about kUploadChunkBytes (at most
+// kUploadChunksMax), the last one cut in halves down to about
+// kUploadTailBytes (few copies, each with a fixed cost on the copy engine, and
+// little work left once the copy has ended). ends[k] is the first plane after
+// chunk k, whose arrival h->up_ev[k] marks. The copies wait for the buffer's
+// earlier readers (kernels on the compute stream).
+int upload_chunks(ecc_handle* h, const void* image, size_t bytes, const Shape& s,
+                  std::vector<int64_t>* ends) {
+  cudaError_t e;
+  if ((e = h->img.ensure(bytes))) return cuda_err(h, e, "image buffer");
+  const int64_t plane = (int64_t)(bytes / (size_t)s.n[0]);
+  const int Keq = (int)std::min<int64_t>(
+      {s.n[0], kUploadChunksMax, std::max<int64_t>(2, (int64_t)(bytes / kUploadChunkBytes))});
+  ends->clear();
+  for (int k = 1; k < Keq; ++k) ends->push_back(s.n[0] * k / Keq);
+  int64_t zt = ends->empty() ? 0 : ends->back();
+  while (s.n[0] - zt >= 2 && (size_t)(s.n[0] - zt) * (size_t)plane > kUploadTailBytes) {
+    zt += (s.n[0] - zt) / 2;
+    ends->push_back(zt);
+  }
+  ends->push_back(s.n[0]);
+  const int K = (int)ends->size();
+  while ((int)h->up_ev.size() < K) {
+    cudaEvent_t ev;
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming))) return cuda_err(h, e, "event");
+    h->up_ev.push_back(ev);
+  }
+  if (!h->up_free && (e = cudaEventCreateWithFlags(&h->up_free, cudaEventDisableTiming)))
+    return cuda_err(h, e, "event");
+  if ((e = cudaEventRecord(h->up_free, h->stream)) ||
+      (e = cudaStreamWaitEvent(h->copy_stream, h->up_free, 0)))
+    return cuda_err(h, e, "order upload");
+  for (int k = 0; k < K; ++k) {
+    const int64_t z0 = k > 0 ? (*ends)[k - 1] : 0, z1 = (*ends)[k];
+    char* dst = static_cast<char*>(h->img.p) + (size_t)(z0 * plane);
+    const char* src = static_cast<const char*>(image) + (size_t)(z0 * plane);
+    if ((e = cudaMemcpyAsync(dst, src, (size_t)((z1 - z0) * plane), cudaMemcpyHostToDevice,
+                             h->copy_stream)) ||
+        (e = cudaEventRecord(h->up_ev[k], h->copy_stream)))
+      return cuda_err(h, e, "copy image");
+  }
+  return ECC_OK;
+}
+
 int enqueue_int(ecc_handle* h, const void* d_img, int64_t row_pitch, const Shape& s, int dtype,
                 int64_t bins, long long* d_vcec, long long* d_curve, cudaStream_t stream,
                 const int64_t* chunk_end, const cudaEvent_t* chunk_ev, int n_chunks) {
@@ -324,7 +369,11 @@ static float key_to_float(uint32_t k) {
   return f;
 }
 
-static int compute_float(ecc_handle* h, const void* d_img, const Shape& s, ecc_result* out) {
+// Float pairs of an image on the device. With n_chunks > 0 the image is still
+// arriving in plane chunks (upload_chunks): the pairs kernel runs per chunk,
+// each launch waiting only for its own chunk (see enqueue_int).
+static int compute_float(ecc_handle* h, const void* d_img, const Shape& s, ecc_result* out,
+                         const int64_t* chunk_end, const cudaEvent_t* chunk_ev, int n_chunks) {
   cudaStream_t st = h->stream;
   const int64_t n = s.voxels;
   cudaError_t e;
@@ -358,7 +407,13 @@ static int compute_float(ecc_handle* h, const void* d_img, const Shape& s, ecc_r
     }
   }
   int64_t cnt = 0;
-  e = launch_local(a, h->num_sms, &cnt);
+  const int K = n_chunks > 0 ? n_chunks : 1;
+  for (int k = 0; k < K && e == cudaSuccess; ++k) {
+    a.w_lo = n_chunks > 0 && k > 0 ? chunk_end[k - 1] - 1 : 0;
+    a.w_hi = n_chunks > 0 && k < K - 1 ? chunk_end[k] - 1 : a.n[0];
+    if (n_chunks > 0 && (e = cudaStreamWaitEvent(st, chunk_ev[k], 0))) break;
+    if (a.w_lo < a.w_hi) e = launch_local(a, h->num_sms, &cnt);
+  }
   if (pa && e == cudaSuccess && (e = cudaEventRecord(pb, st)) == cudaSuccess) {
     h->prof_events.emplace_back(pa, pb);
   } else if (pa) {
@@ -564,14 +619,19 @@ int ecc_compute(ecc_handle* h, const void* image, const int64_t* dims, int ndim,
         return ECC_OK;
       }
       const void* d_img = image;
-      if (!on_dev) {
-        if ((e = h->img.ensure(eb * s.voxels))) return cuda_err(h, e, "image buffer");
-        if ((e = cudaMemcpyAsync(h->img.p, image, eb * s.voxels, cudaMemcpyHostToDevice,
-                                 h->stream)))
+      const size_t fbytes = eb * (size_t)s.voxels;
+      std::vector<int64_t> ends;
+      if (!on_dev && fbytes >= kChunkedUploadBytes && s.n[0] >= 2) {
+        // chunked upload overlapping the pairs kernel, as for integer images
+        if ((rc = upload_chunks(h, image, fbytes, s, &ends))) return rc;
+        d_img = h->img.p;
+      } else if (!on_dev) {
+        if ((e = h->img.ensure(fbytes))) return cuda_err(h, e, "image buffer");
+        if ((e = cudaMemcpyAsync(h->img.p, image, fbytes, cudaMemcpyHostToDevice, h->stream)))
           return cuda_err(h, e, "copy image");
         d_img = h->img.p;
       }
-      rc = compute_float(h, d_img, s, out);
+      rc = compute_float(h, d_img, s, out, ends.data(), h->up_ev.data(), (int)ends.size());
       if (rc) ecc_result_free(out);
       return rc;
     }
@@ -586,42 +646,9 @@ int ecc_compute(ecc_handle* h, const void* image, const int64_t* dims, int ndim,
       // large host image: upload in plane chunks on the copy stream and start
       // each chunk's kernels as soon as it (and the next chunk's first plane)
       // has arrived, so the copy and the computation overlap
-      if ((e = h->img.ensure(bytes))) return cuda_err(h, e, "image buffer");
-      const int64_t plane = (int64_t)(bytes / (size_t)s.n[0]);
-      const int Keq = (int)std::min<int64_t>(
-          {s.n[0], kUploadChunksMax, std::max<int64_t>(2, (int64_t)(bytes / kUploadChunkBytes))});
-      // equal chunks of about kUploadChunkBytes, the last one cut in halves
-      // down to about kUploadTailBytes: few copies (each has a fixed cost on
-      // the copy engine) and little work left once the copy has ended
       std::vector<int64_t> ends;
-      for (int k = 1; k < Keq; ++k) ends.push_back(s.n[0] * k / Keq);
-      int64_t zt = ends.empty() ? 0 : ends.back();
-      while (s.n[0] - zt >= 2 && (size_t)(s.n[0] - zt) * (size_t)plane > kUploadTailBytes) {
-        zt += (s.n[0] - zt) / 2;
-        ends.push_back(zt);
-      }
-      ends.push_back(s.n[0]);
+      if ((rc = upload_chunks(h, image, bytes, s, &ends))) return rc;
       const int K = (int)ends.size();
-      while ((int)h->up_ev.size() < K) {
-        cudaEvent_t ev;
-        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming))) return cuda_err(h, e, "event");
-        h->up_ev.push_back(ev);
-      }
-      if (!h->up_free && (e = cudaEventCreateWithFlags(&h->up_free, cudaEventDisableTiming)))
-        return cuda_err(h, e, "event");
-      // the buffer's earlier readers (kernels on the compute stream) first
-      if ((e = cudaEventRecord(h->up_free, h->stream)) ||
-          (e = cudaStreamWaitEvent(h->copy_stream, h->up_free, 0)))
-        return cuda_err(h, e, "order upload");
-      for (int k = 0; k < K; ++k) {
-        const int64_t z0 = k > 0 ? ends[k - 1] : 0, z1 = ends[k];
-        char* dst = static_cast<char*>(h->img.p) + (size_t)(z0 * plane);
-        const char* src = static_cast<const char*>(image) + (size_t)(z0 * plane);
-        if ((e = cudaMemcpyAsync(dst, src, (size_t)((z1 - z0) * plane), cudaMemcpyHostToDevice,
-                                 h->copy_stream)) ||
-            (e = cudaEventRecord(h->up_ev[k], h->copy_stream)))
-          return cuda_err(h, e, "copy image");
-      }
       rc = enqueue_int(h, h->img.p, 0, s, dtype, bins, h->vcec.as<long long>(),
                        h->curve.as<long long>(), h->stream, ends.data(), h->up_ev.data(), K);
     } else {

@@ -150,6 +150,28 @@ def test_f32_4d_full_size_equals_oracle(tmp_path, conv):
 
 
 @pytest.mark.parametrize("conv", ["V", "T"])
+@pytest.mark.parametrize("shape", [(20, 48, 64, 72), (70, 240, 256)], ids=str)
+def test_f32_host_image_chunked_upload(tmp_path, conv, shape):
+    """Float images of 16 MB or more in host memory are uploaded in plane
+    chunks while the pairs kernel runs on the chunks already there: the pairs
+    equal the oracle's (4D and 3D, both conventions)."""
+    import oracle_pool
+    img = synth.grf_f32(shape, 2.0, S + 59)
+    assert img.nbytes >= 16 << 20
+    h = ecc.ecc_create(device=0, convention=ecc.ECC_CONV_V if conv == "V" else ecc.ECC_CONV_T)
+    try:
+        t, chi = ecc.ecc_compute(h, img)
+        t2, chi2 = ecc.ecc_compute(h, img)  # the buffer reused after its readers
+    finally:
+        ecc.ecc_destroy(h)
+    path = tmp_path / "f.raw"
+    img.tofile(path)
+    t_ref, chi_ref = oracle_pool.ecc_pairs_float_parallel(path, shape, 4, conv=conv)
+    assert np.array_equal(t, t_ref) and np.array_equal(chi, chi_ref)
+    assert np.array_equal(t2, t_ref) and np.array_equal(chi2, chi_ref)
+
+
+@pytest.mark.parametrize("conv", ["V", "T"])
 def test_f32_4d_noise_past_1024_radix_tiles(tmp_path, conv):
     """4D i.i.d. uniform floats, 64^4: more than half the voxels carry a
     non-zero change, so the (key, change) pairs exceed 1024 radix tiles of

@@ -339,10 +339,34 @@ def bench_batched(h, reqs, stream):
     def batched():
         return ecc.ecc_compute_batch(h, dev, bins)
 
+    # the C call alone, its image descriptors built once (as a caller
+    # reusing them would), the results released after the timing
+    import ctypes as C
+    lib = ecc.load()
+    n = len(dev)
+    descs = (ecc.ecc_image * n)()
+    for i, (d, b) in enumerate(zip(dev, bins)):
+        descs[i].data = d.data_ptr()
+        for j, sz in enumerate(d.shape):
+            descs[i].dims[j] = int(sz)
+        descs[i].ndim = d.dim()
+        descs[i].dtype = ecc.ECC_U8 if d.dtype == torch.uint8 else ecc.ECC_U16
+        descs[i].bins = int(b)
+    outs = (ecc.ecc_result * n)()
+
+    def batched_c():
+        t0 = time.perf_counter()
+        assert lib.ecc_compute_batch(h, n, descs, outs) == ecc.ECC_OK
+        dt = time.perf_counter() - t0
+        for i in range(n):
+            lib.ecc_result_free(C.byref(outs[i]))
+        return dt
+
     per_image()
     batched()
+    batched_c()
     torch.cuda.synchronize()
-    t_per, t_bat = [], []
+    t_per, t_bat, t_c, k_ms = [], [], [], []
     for _ in range(3):
         t0 = time.perf_counter()
         ref = per_image()
@@ -350,12 +374,26 @@ def bench_batched(h, reqs, stream):
         t0 = time.perf_counter()
         res = batched()
         t_bat.append(time.perf_counter() - t0)
+        ecc.ecc_set_profiling(h, True)
+        ecc.ecc_profile_read(h)
+        t_c.append(batched_c())
+        ecc.ecc_profile_read(h)
+        ecc.ecc_set_profiling(h, False)
+        k_ms.append(ecc.ecc_profile_span(h))
     same = all(np.array_equal(r.numpy(), b) for r, b in zip(ref, res))
     assert same, "batched curves differ from per-image curves"
-    tp, tb = min(t_per), min(t_bat)
+    tp, tb, tc = min(t_per), min(t_bat), min(t_c)
+    kernel_s = k_ms[int(np.argmin(t_c))] / 1e3
     return {"images": len(reqs), "voxels": int(vox), "per_image_s": tp, "batched_s": tb,
             "speedup": tp / tb, "gvox_s_batched": vox / tb / 1e9,
-            "gvox_s_per_image": vox / tp / 1e9, "identical": bool(same)}
+            "gvox_s_per_image": vox / tp / 1e9, "identical": bool(same),
+            "c_call_s": tc, "graphs_span_s": kernel_s, "c_call_over_graphs": tc / kernel_s,
+            "timing": "per_image_s / batched_s: the Python calls (ecc_compute_device per "
+                      "image then each curve to the host / ecc_compute_batch with its "
+                      "argument marshalling and curve views), best of 3; c_call_s: "
+                      "ecc_compute_batch itself with prepared descriptors; graphs_span_s: the "
+                      "device time from the first of its batched graphs' start to the last "
+                      "one's end (profiling events; the two slots' graphs overlap)"}
 
 
 def bench_serving(h, reqs, rate_hz: float, seed: int, borrowed: bool = False):

@@ -80,8 +80,11 @@ typedef struct ecc_config {
 /* Result of one image. Integer images: curve[t] = chi(K_t), t < bins.
  * Float images: the (threshold, chi) pairs at every value t where the VCEC
  * is non-zero, ascending in t; the curve is constant between them and 0 below
- * the first. Arrays are allocated by the library (owned = 1) and released
- * with ecc_result_free. */
+ * the first. Arrays are allocated by the library (owned = 1), or, for the
+ * curves of ecc_compute_batch, lie in a pinned host block of the library
+ * shared by a batch's results (owned = 2); either way they are released with
+ * ecc_result_free (a shared block once all its results are released, also
+ * after ecc_destroy). */
 typedef struct ecc_result {
   int64_t bins;
   int64_t* curve;
@@ -202,9 +205,12 @@ int ecc_stream_file(ecc_handle* h, const char* path, int64_t offset, const int64
                     int ndim, ecc_dtype dtype, ecc_result* out);
 
 /* Batched computation: all images of the batch in one persistent launch
- * whose blocks take (image, tile) items from a work list. Images of any
- * ndim/dtype (integer dtypes), host or device pointers; outs[i] receives
- * image i's curve and outs[i].status its status. Blocks until done. */
+ * whose blocks take (image, tile) items from a work list (batches of more
+ * than 1024 images run in launches of 1024, each built while the previous
+ * one runs). Images of 1-3 dimensions and integer dtypes, host or device
+ * pointers (a device image aligned to its element size); outs[i] receives
+ * image i's curve (owned = 2: see ecc_result) and outs[i].status its status.
+ * Blocks until done. */
 int ecc_compute_batch(ecc_handle* h, int n, const ecc_image* images, ecc_result* outs);
 
 /* Serving: queues one request. The image (integer dtype; pageable or pinned
@@ -253,11 +259,18 @@ int64_t ecc_launch_count(const ecc_handle* h);
 
 /* Instrumentation (no counterpart in the paper). With profiling on, every
  * single-image computation (integer curve or float pairs) records CUDA events
- * on its launching stream around its contribution kernel(s). ecc_profile_read synchronises, returns the summed
+ * on its launching stream around its contribution kernel(s), and every
+ * launch of ecc_compute_batch around its graph (clear, contribution, scan). ecc_profile_read synchronises, returns the summed
  * elapsed milliseconds and the number of computations recorded since the
  * last read, and clears the record. */
 int ecc_set_profiling(ecc_handle* h, int on);
 int ecc_profile_read(ecc_handle* h, double* contrib_ms, int64_t* count);
+
+/* Milliseconds from the earliest start to the latest end among the event
+ * pairs of the record the last ecc_profile_read returned: the device time
+ * the recorded work spanned, work that overlapped (the two slots of a batched
+ * computation) counted once. */
+int ecc_profile_span(ecc_handle* h, double* span_ms);
 
 /* ECC of an integer image already on the device, for callers that cannot
  * allocate device memory: for example a host program that has handed all of

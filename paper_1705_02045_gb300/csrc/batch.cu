@@ -64,8 +64,6 @@ struct BHeader {
 };
 
 constexpr int kMaxBatch = 1024;
-constexpr size_t kParallelResultBytes = size_t(8) << 20;  // curves copied out by kResultThreads
-constexpr size_t kResultThreads = 4;
 constexpr int64_t kSmallBins = 256;
 constexpr int kBatchBitsWarps = 8;
 constexpr int kBatchPlRec = 17;  // odd and >= 16 + 1 planes
@@ -292,6 +290,8 @@ struct Slot {
   cudaEvent_t done = nullptr;
   cudaEvent_t t0 = nullptr, t1 = nullptr;  // around the graph, for the online tuner
   std::vector<size_t> res_off;             // byte offset of each image's curve in h_arena
+  std::vector<ResultBlock*> blocks;        // result blocks of ecc_compute_batch (one
+                                           // reference each held by the slot)
   int tune_cand = -1;                      // candidate timed by the last run, or -1
   double tune_vox = 0;                     // its bit-sliced voxels
 };
@@ -315,6 +315,7 @@ struct BatchTune {
 struct BatchEngine {
   std::vector<Slot> slots;
   BatchTune tune;
+  cudaEvent_t staged = nullptr;  // ecc_compute_batch: host images staged on slot 0's stream
   BatchEngine() {
     if (const char* z = std::getenv("ECC_BATCH_ZC")) tune.fixed = std::max(0, std::atoi(z));
   }
@@ -412,6 +413,8 @@ void slot_free(Slot& sl) {
   if (sl.h_desc) cudaFreeHost(sl.h_desc);
   if (sl.h_arena) cudaFreeHost(sl.h_arena);
   for (unsigned char* p : sl.h_retired) cudaFreeHost(p);
+  for (ResultBlock* b : sl.blocks) result_block_release(b);
+  sl.blocks.clear();
   sl.desc.release();
   sl.arena.release();
   sl.staging.release();
@@ -506,7 +509,7 @@ void untune_depth(BatchTune& t, Slot& sl) {
 // offsets sl.res_off (results_bytes(specs) bytes); null = the slot's own
 // pinned arena.
 int slot_run(ecc_handle* h, Slot& sl, BatchTune& tune, const std::vector<ImgSpec>& specs,
-             cudaEvent_t wait_ev, unsigned char* h_res = nullptr) {
+             cudaEvent_t wait_ev, unsigned char* h_res = nullptr, bool profile = false) {
   cudaError_t e;
   const int n = (int)specs.size();
   int depth = tune_depth(tune, sl);
@@ -532,14 +535,15 @@ int slot_run(ecc_handle* h, Slot& sl, BatchTune& tune, const std::vector<ImgSpec
   bool large = false;
   // device arena: all VCECs, then all (curve, error word) records, so that
   // only the second part is copied back
+  // (each record: a 16-byte header the host fills, the curve, the error word)
   size_t vcec_total = 0, res_total = 0;
   sl.res_off.resize(n);
   for (int i = 0; i < n; ++i) {
     const ImgSpec& sp = specs[i];
     if (sp.bins > kSmallBins && sp.bins <= kSmemBinsMax) large = true;
     vcec_total += sizeof(long long) * sp.bins;
-    sl.res_off[i] = res_total;
-    res_total += sizeof(long long) * (sp.bins + 1);
+    sl.res_off[i] = res_total + kResultHeader;
+    res_total += kResultHeader + sizeof(long long) * (sp.bins + 1);
   }
   // Arenas grow geometrically and without waiting for the device: the device
   // one in stream order on the slot's stream (a plain free would wait for
@@ -630,9 +634,23 @@ int slot_run(ecc_handle* h, Slot& sl, BatchTune& tune, const std::vector<ImgSpec
                                     : capture_graph<kConvV>(sl, large, &ex);
     if (e) return cuda_err(h, e, "capture batch graph");
   }
-  if ((e = cudaEventRecord(sl.t0, sl.stream)) || (e = cudaGraphLaunch(ex, sl.stream)) ||
-      (e = cudaEventRecord(sl.t1, sl.stream)))
+  // instrumentation (profile): an event pair of the handle's profiling record
+  // around the graph
+  cudaEvent_t pa = nullptr, pb = nullptr;
+  if (profile && (cudaEventCreate(&pa) != cudaSuccess || cudaEventCreate(&pb) != cudaSuccess)) {
+    if (pa) cudaEventDestroy(pa);
+    if (pb) cudaEventDestroy(pb);
+    pa = pb = nullptr;
+    cudaGetLastError();
+  }
+  if ((e = cudaEventRecord(sl.t0, sl.stream)) || (pa && (e = cudaEventRecord(pa, sl.stream))) ||
+      (e = cudaGraphLaunch(ex, sl.stream)) || (pb && (e = cudaEventRecord(pb, sl.stream))) ||
+      (e = cudaEventRecord(sl.t1, sl.stream))) {
+    if (pa) cudaEventDestroy(pa);
+    if (pb) cudaEventDestroy(pb);
     return cuda_err(h, e, "graph launch");
+  }
+  if (pa) h->prof_events.emplace_back(pa, pb);
   h->launches += 4;
   if (sl.tune_cand >= 0) {
     if (bits_vox > 0) sl.tune_vox = bits_vox;
@@ -645,10 +663,10 @@ int slot_run(ecc_handle* h, Slot& sl, BatchTune& tune, const std::vector<ImgSpec
   return ECC_OK;
 }
 
-// Bytes of the (curve, error word) records of a batch.
+// Bytes of the (header, curve, error word) records of a batch.
 size_t results_bytes(const std::vector<ImgSpec>& specs) {
   size_t t = 0;
-  for (const ImgSpec& sp : specs) t += sizeof(long long) * (sp.bins + 1);
+  for (const ImgSpec& sp : specs) t += kResultHeader + sizeof(long long) * (sp.bins + 1);
   return t;
 }
 
@@ -657,18 +675,6 @@ int record_status(const long long* rec, int64_t bins) {
   const int err = *reinterpret_cast<const int*>(rec + bins);
   if (err & kErrValue) return ECC_ERR_VALUE;
   if (err & kErrOverflow) return ECC_ERR_CUDA;
-  return ECC_OK;
-}
-
-// Image i's curve out of the slot's pinned arena; status from its error word.
-int slot_result(const Slot& sl, const std::vector<ImgSpec>& specs, int i, int64_t** curve) {
-  const long long* rec = reinterpret_cast<const long long*>(sl.h_arena + sl.res_off[i]);
-  const int64_t bins = specs[i].bins;
-  const int st = record_status(rec, bins);
-  if (st != ECC_OK) return st;
-  *curve = static_cast<int64_t*>(std::malloc(sizeof(int64_t) * std::max<int64_t>(bins, 1)));
-  if (!*curve) return ECC_ERR_OOM;
-  std::memcpy(*curve, rec, sizeof(int64_t) * bins);
   return ECC_OK;
 }
 
@@ -1462,6 +1468,7 @@ void serve_shutdown(ecc_handle* h) {
   }
   if (h->batch) {
     for (Slot& sl : h->batch->slots) slot_free(sl);
+    if (h->batch->staged) cudaEventDestroy(h->batch->staged);
     delete h->batch;
     h->batch = nullptr;
   }
@@ -1487,10 +1494,12 @@ int ecc_compute_batch(ecc_handle* h, int n, const ecc_image* images, ecc_result*
     }
     if (!h->batch) {
       h->batch = new BatchEngine();
-      h->batch->slots.resize(1);
-      int rc = slot_init(h, h->batch->slots[0], true);
+      h->batch->slots.resize(2);
+      int rc = ECC_OK;
+      for (Slot& s2 : h->batch->slots)
+        if (!rc) rc = slot_init(h, s2, true);
       if (rc) {
-        slot_free(h->batch->slots[0]);
+        for (Slot& s2 : h->batch->slots) slot_free(s2);
         delete h->batch;
         h->batch = nullptr;
         return rc;
@@ -1501,6 +1510,7 @@ int ecc_compute_batch(ecc_handle* h, int n, const ecc_image* images, ecc_result*
     std::vector<ImgSpec> all(n);
     std::vector<int> ok(n, 0);
     std::vector<size_t> stage_off(n, SIZE_MAX);
+    std::vector<char> on_dev(n, 0);
     size_t staged = 0;
     for (int i = 0; i < n; ++i) {
       const ecc_image& im = images[i];
@@ -1526,6 +1536,7 @@ int ecc_compute_batch(ecc_handle* h, int n, const ecc_image* images, ecc_result*
       // images are read in place (the kernels take rows at any alignment)
       const int64_t pitch = staged_pitch(h, im.dtype, bins, sp.n[2]);
       const bool dev = is_device_ptr(h, im.data);
+      on_dev[i] = dev;
       if (dev && !elem_aligned(im.data, im.dtype)) {
         outs[i].status = set_err(h, ECC_ERR_ARG, "device image not aligned to its element size");
         ok[i] = 0;
@@ -1544,52 +1555,101 @@ int ecc_compute_batch(ecc_handle* h, int n, const ecc_image* images, ecc_result*
         ImgSpec& sp = all[i];
         const size_t dense = dtype_bytes(sp.dtype) * (size_t)sp.n[2];
         char* d = static_cast<char*>(sl.staging.p) + stage_off[i];
-        const cudaMemcpyKind kind = is_device_ptr(h, images[i].data) ? cudaMemcpyDeviceToDevice
-                                                                      : cudaMemcpyHostToDevice;
+        const cudaMemcpyKind kind = on_dev[i] ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
         if ((e = cudaMemcpy2DAsync(d, (size_t)sp.row_pitch, images[i].data, dense, dense,
                                    (size_t)(sp.n[0] * sp.n[1]), kind, sl.stream)))
           return cuda_err(h, e, "copy batch image");
         sp.d_img = d;
       }
     }
-    // run in chunks of kMaxBatch valid images
+    // the second slot's launches read the staged images too
+    cudaEvent_t staged_ev = nullptr;
+    if (staged) {
+      BatchEngine* be = h->batch;
+      if (!be->staged && (e = cudaEventCreateWithFlags(&be->staged, cudaEventDisableTiming)))
+        return cuda_err(h, e, "event");
+      if ((e = cudaEventRecord(be->staged, sl.stream))) return cuda_err(h, e, "record");
+      staged_ev = be->staged;
+    }
+    // Chunks of kMaxBatch valid images alternate between the two slots: a
+    // chunk's work list is built and launched while the previous chunk runs.
+    // Results stay where the copy back put them, in a pinned block of the
+    // slot: each curve is handed out in place (owned = 2) and the block is
+    // reused once all of them have been freed.
     std::vector<int> idx;
     for (int i = 0; i < n; ++i)
       if (ok[i]) idx.push_back(i);
-    for (size_t c0 = 0; c0 < idx.size(); c0 += kMaxBatch) {
-      const size_t c1 = std::min(idx.size(), c0 + kMaxBatch);
+    struct Pending {
+      bool active = false;
+      size_t c0 = 0, c1 = 0;
       std::vector<ImgSpec> specs;
-      for (size_t j = c0; j < c1; ++j) specs.push_back(all[idx[j]]);
-      int rc = slot_run(h, sl, h->batch->tune, specs, nullptr);
-      if (!rc) rc = wait_event(h, sl.done, 300LL * 1000 * 1000);
+      ResultBlock* blk = nullptr;
+    } pend[2];
+    auto finish = [&](int si) -> int {
+      Pending& pd = pend[si];
+      if (!pd.active) return ECC_OK;
+      pd.active = false;
+      Slot& s2 = h->batch->slots[si];
+      const int rc = wait_event(h, s2.done, 300LL * 1000 * 1000);
       if (rc) return rc;
-      // curves out of the pinned arena; many megabytes of them are split
-      // over a few threads (each curve its own allocation, as the caller
-      // frees them one by one)
-      auto take = [&](size_t a, size_t b) {
-        for (size_t j = a; j < b; ++j) {
-          ecc_result& o = outs[idx[j]];
-          o.status = slot_result(sl, specs, (int)(j - c0), &o.curve);
-          o.bins = o.status == ECC_OK ? specs[j - c0].bins : 0;
-        }
-      };
-      size_t res_bytes = 0;
-      for (const ImgSpec& sp : specs) res_bytes += sizeof(int64_t) * (size_t)sp.bins;
-      const size_t nt = res_bytes >= kParallelResultBytes ? kResultThreads : 1;
-      std::vector<std::thread> helpers;
-      size_t done_to = c0;
-      try {
-        for (size_t t = 1; t < nt; ++t) {
-          const size_t a = c0 + (c1 - c0) * t / nt, b = c0 + (c1 - c0) * (t + 1) / nt;
-          helpers.emplace_back(take, a, b);
-          done_to = b;
-        }
-      } catch (const std::system_error&) {
-        // no thread: this one copies the rest
+      for (size_t j = pd.c0; j < pd.c1; ++j) {
+        const ImgSpec& sp = pd.specs[j - pd.c0];
+        unsigned char* rec = pd.blk->p + s2.res_off[j - pd.c0];
+        ecc_result& o = outs[idx[j]];
+        o.status = record_status(reinterpret_cast<const long long*>(rec), sp.bins);
+        if (o.status != ECC_OK) continue;
+        uint64_t* hdr = reinterpret_cast<uint64_t*>(rec) - 2;
+        hdr[0] = reinterpret_cast<uint64_t>(pd.blk);
+        hdr[1] = kResultMagic;
+        pd.blk->refs.fetch_add(1, std::memory_order_relaxed);
+        o.curve = reinterpret_cast<int64_t*>(rec);
+        o.bins = sp.bins;
+        o.owned = 2;
       }
-      take(c0, helpers.empty() ? c1 : c0 + (c1 - c0) / nt);
-      for (std::thread& t : helpers) t.join();
-      if (done_to < c1 && !helpers.empty()) take(done_to, c1);
+      return ECC_OK;
+    };
+    // a block of the slot that no result refers to any more, else a new one
+    auto take_block = [&](Slot& s2, size_t need) -> ResultBlock* {
+      for (size_t b = 0; b < s2.blocks.size(); ++b) {
+        ResultBlock* blk = s2.blocks[b];
+        if (blk->refs.load(std::memory_order_acquire) != 1) continue;
+        if (blk->cap >= need) return blk;
+        result_block_release(blk);  // too small and unused: drop it
+        s2.blocks.erase(s2.blocks.begin() + (long)b);
+        --b;
+      }
+      ResultBlock* blk = new ResultBlock();
+      const size_t cap = std::max(need + need / 4, size_t(1) << 20);
+      if (cudaMallocHost(&blk->p, cap) != cudaSuccess) {
+        cudaGetLastError();
+        delete blk;
+        return nullptr;
+      }
+      blk->cap = cap;
+      s2.blocks.push_back(blk);
+      return blk;
+    };
+    size_t chunk = 0;
+    for (size_t c0 = 0; c0 < idx.size(); c0 += kMaxBatch, ++chunk) {
+      const int si = (int)(chunk & 1);
+      int rc = finish(si);  // the slot's previous chunk
+      if (rc) return rc;
+      Slot& s2 = h->batch->slots[si];
+      Pending& pd = pend[si];
+      pd.c0 = c0;
+      pd.c1 = std::min(idx.size(), c0 + kMaxBatch);
+      pd.specs.clear();
+      for (size_t j = pd.c0; j < pd.c1; ++j) pd.specs.push_back(all[idx[j]]);
+      pd.blk = take_block(s2, results_bytes(pd.specs));
+      if (!pd.blk) return set_err(h, ECC_ERR_OOM, "pinned result block");
+      rc = slot_run(h, s2, h->batch->tune, pd.specs, si == 0 ? nullptr : staged_ev, pd.blk->p,
+                    h->prof_on);
+      if (rc) return rc;
+      pd.active = true;
+    }
+    for (int si = 0; si < 2; ++si) {
+      const int rc = finish(si);
+      if (rc) return rc;
     }
     return ECC_OK;
   } catch (const std::bad_alloc&) {

@@ -159,6 +159,14 @@ constexpr size_t kUploadTailBytes = size_t(2) << 20;
 // little work left once the copy has ended). ends[k] is the first plane after
 // chunk k, whose arrival h->up_ev[k] marks. The copies wait for the buffer's
 // earlier readers (kernels on the compute stream).
+void result_block_release(ResultBlock* b) {
+  if (b && b->refs.fetch_sub(1, std::memory_order_acq_rel) == 1) {
+    cudaFreeHost(b->p);
+    cudaGetLastError();
+    delete b;
+  }
+}
+
 int upload_chunks(ecc_handle* h, const void* image, size_t bytes, const Shape& s,
                   std::vector<int64_t>* ends) {
   cudaError_t e;
@@ -576,7 +584,15 @@ const char* ecc_last_error(const ecc_handle* h) {
 
 void ecc_result_free(ecc_result* r) {
   if (!r) return;
-  if (r->owned) {
+  if (r->owned == 2) {
+    // a curve inside a batch's pinned result block: drop its reference
+    if (r->curve) {
+      const uint64_t* hdr = reinterpret_cast<const uint64_t*>(r->curve) - 2;
+      if (hdr[1] == kResultMagic) result_block_release(reinterpret_cast<ResultBlock*>(hdr[0]));
+    }
+    std::free(r->thresholds);
+    std::free(r->chi);
+  } else if (r->owned) {
     std::free(r->curve);
     std::free(r->thresholds);
     std::free(r->chi);
@@ -830,23 +846,40 @@ int ecc_set_profiling(ecc_handle* h, int on) {
 int ecc_profile_read(ecc_handle* h, double* contrib_ms, int64_t* count) {
   if (!h || !contrib_ms || !count) return ECC_ERR_ARG;
   std::lock_guard<std::mutex> lk(h->api_mu);
-  double total = 0.0;
+  double total = 0.0, lo = 0.0, hi = 0.0;
   int rc = ECC_OK;
-  for (auto& pr : h->prof_events) {
-    if (rc == ECC_OK) rc = wait_event(h, pr.second, 300LL * 1000 * 1000);
-    float ms = 0.f;
+  const auto& ev = h->prof_events;
+  for (size_t i = 0; i < ev.size(); ++i) {
+    if (rc == ECC_OK) rc = wait_event(h, ev[i].second, 300LL * 1000 * 1000);
+    float ms = 0.f, a = 0.f, b = 0.f;
     if (rc == ECC_OK) {
-      cudaError_t e = cudaEventElapsedTime(&ms, pr.first, pr.second);
+      // this pair's duration, and its start and end relative to the first
+      // pair's start (for the span the recorded work covered)
+      cudaError_t e = cudaEventElapsedTime(&ms, ev[i].first, ev[i].second);
+      if (!e && i > 0) e = cudaEventElapsedTime(&a, ev[0].first, ev[i].first);
+      if (!e) b = a + ms;
       if (e) rc = cuda_err(h, e, "elapsed time");
     }
     total += ms;
+    lo = i == 0 ? a : std::min(lo, (double)a);
+    hi = i == 0 ? b : std::max(hi, (double)b);
+  }
+  for (auto& pr : h->prof_events) {
     cudaEventDestroy(pr.first);
     cudaEventDestroy(pr.second);
   }
   *count = (int64_t)h->prof_events.size();
   h->prof_events.clear();
   *contrib_ms = total;
+  h->prof_span_ms = rc == ECC_OK ? hi - lo : 0.0;
   return rc;
+}
+
+int ecc_profile_span(ecc_handle* h, double* span_ms) {
+  if (!h || !span_ms) return ECC_ERR_ARG;
+  std::lock_guard<std::mutex> lk(h->api_mu);
+  *span_ms = h->prof_span_ms;
+  return ECC_OK;
 }
 
 }  // extern "C"

@@ -50,6 +50,21 @@ struct Shape {
   int64_t n[4] = {1, 1, 1, 1};
 };
 
+// Pinned host memory holding the curves of one batched computation, which
+// the results of ecc_compute_batch point into (ecc_result.owned = 2) instead
+// of owning a copy. Each curve is preceded by a 16-byte header: the block's
+// address and kResultMagic. refs counts the results still alive plus one
+// while the handle keeps the block for reuse; the last release frees it.
+struct ResultBlock {
+  unsigned char* p = nullptr;
+  size_t cap = 0;
+  std::atomic<int64_t> refs{1};
+};
+constexpr uint64_t kResultMagic = 0x45434342524c4b31ull;  // "ECCBRLK1"
+constexpr size_t kResultHeader = 16;
+// Drops one reference; frees the block's memory with the last one.
+void result_block_release(ResultBlock* b);
+
 struct BatchEngine;  // batch.cu
 struct Server;       // batch.cu
 
@@ -104,6 +119,7 @@ struct ecc_handle {
 
   // instrumentation: event pairs around contribution kernels
   bool prof_on = false;
+  double prof_span_ms = 0.0;           // span of the record read last (ecc_profile_span)
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
 
   // batched launches and serving (batch.cu)

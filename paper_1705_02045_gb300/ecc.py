@@ -75,6 +75,7 @@ _SIGNATURES = {
     "ecc_launch_count": (C.c_int64, [_P]),
     "ecc_set_profiling": (C.c_int, [_P, C.c_int]),
     "ecc_profile_read": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "ecc_profile_span": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "ecc_compute_device_noalloc": (C.c_int, [_P, _I64P, C.c_int, C.c_int, C.c_int64, C.c_int,
                                              _P, _P]),
 }
@@ -108,14 +109,21 @@ def load(build_if_missing: bool = False):
     return lib
 
 
+_DTYPE_CODES = {}
+
+
 def _dtype_code(dt) -> int:
     """ECC dtype code of a numpy dtype / scalar type or a torch dtype; other
     types map to 0, which the library rejects with ECC_ERR_DTYPE."""
-    try:
-        name = np.dtype(dt).name
-    except TypeError:
-        name = str(dt).replace("torch.", "")
-    return {"uint8": ECC_U8, "uint16": ECC_U16, "float32": ECC_F32}.get(name, 0)
+    code = _DTYPE_CODES.get(dt)
+    if code is None:
+        try:
+            name = np.dtype(dt).name
+        except TypeError:
+            name = str(dt).replace("torch.", "")
+        code = {"uint8": ECC_U8, "uint16": ECC_U16, "float32": ECC_F32}.get(name, 0)
+        _DTYPE_CODES[dt] = code
+    return code
 
 
 def _check(h, rc: int) -> int:
@@ -322,11 +330,12 @@ def ecc_compute_batch(h, images, bins=None):
     _check(h, lib.ecc_compute_batch(h, n, descs, outs))
     res = []
     for i in range(n):
-        if outs[i].status != ECC_OK:
-            res.append(EccError(outs[i].status, f"image {i}"))
+        o = outs[i]
+        if o.status != ECC_OK:
+            res.append(EccError(o.status, f"image {i}"))
+            lib.ecc_result_free(C.byref(o))
         else:
-            res.append(_result_to_numpy(outs[i]))
-        lib.ecc_result_free(C.byref(outs[i]))
+            res.append(_result_to_numpy(o))  # takes the buffers over
     return res
 
 
@@ -394,6 +403,13 @@ def ecc_profile_read(h):
     ms, n = C.c_double(), C.c_int64()
     _check(h, load().ecc_profile_read(h, C.byref(ms), C.byref(n)))
     return ms.value, n.value
+
+
+def ecc_profile_span(h) -> float:
+    """Device milliseconds spanned by the record the last ecc_profile_read returned."""
+    ms = C.c_double()
+    _check(h, load().ecc_profile_span(h, C.byref(ms)))
+    return ms.value
 
 
 def ecc_compute_device_noalloc(d_image, bins: int, d_curve, convention: int = ECC_CONV_V,

@@ -225,6 +225,59 @@ def test_batch_more_than_one_launch_worth(lib):
         assert np.array_equal(r, oracle.ecc_int(img, 256, "V"))
 
 
+def test_batch_results_live_in_shared_blocks(lib):
+    """2500 images (three launches of up to 1024, alternating between the two
+    slots; host images staged once and read by both): the curves of three
+    calls kept alive together (each call's results in pinned blocks the
+    library shares between them), then the first call's dropped and the
+    blocks reused by a fourth call; every curve is the oracle's, also after
+    the handle is destroyed."""
+    import torch
+    rng = np.random.default_rng(S + 14)
+    imgs, bins = [], []
+    for i in range(2500):
+        shape = tuple(int(x) for x in rng.integers(1, 10, size=int(rng.integers(1, 4))))
+        if i % 3 == 0:
+            imgs.append(rng.integers(0, 16384, size=shape).astype(np.uint16))
+            bins.append(16384)
+        else:
+            imgs.append(rng.integers(0, 256, size=shape).astype(np.uint8))
+            bins.append(256)
+    want = [oracle.ecc_int(img, b, "V") for img, b in zip(imgs, bins)]
+    arrays = [torch.from_numpy(a).cuda() if i % 11 == 0 else a for i, a in enumerate(imgs)]
+    h = ecc.ecc_create(device=0)
+    try:
+        kept = [ecc.ecc_compute_batch(h, arrays, bins) for _ in range(3)]
+        for res in kept:
+            assert all(np.array_equal(r, w) for r, w in zip(res, want))
+        del kept[0]
+        kept.append(ecc.ecc_compute_batch(h, arrays, bins))
+    finally:
+        ecc.ecc_destroy(h)
+    for res in kept:
+        assert len(res) == len(want)
+        assert all(np.array_equal(r, w) for r, w in zip(res, want))
+
+
+def test_batch_profiling_records_graphs(lib):
+    """With profiling on, a batched call records its graphs: the span from the
+    first start to the last end is positive and at most their summed time
+    plus the gaps (the two slots' graphs overlap or follow each other)."""
+    rng = np.random.default_rng(S + 15)
+    imgs = [rng.integers(0, 256, size=(12, 40, 64), dtype=np.uint8) for _ in range(1500)]
+    h = ecc.ecc_create(device=0)
+    try:
+        ecc.ecc_set_profiling(h, True)
+        ecc.ecc_profile_read(h)
+        res = ecc.ecc_compute_batch(h, imgs)
+        total, count = ecc.ecc_profile_read(h)
+        span = ecc.ecc_profile_span(h)
+    finally:
+        ecc.ecc_destroy(h)
+    assert count == 2 and total > 0 and 0 < span
+    assert np.array_equal(res[0], oracle.ecc_int(imgs[0], 256, "V"))
+
+
 # ---- serving ----------------------------------------------------------------
 
 def test_serve_alone_equals_in_the_mix(lib):

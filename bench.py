@@ -433,10 +433,18 @@ def bench_serving(h, reqs, rate_hz: float, seed: int, borrowed: bool = False):
         assert st == ecc.ECC_OK
     wall = time.perf_counter() - t0
     lat = np.array([ecc.ecc_request_latency_us(h, rid) for rid in ids]) / 1e3
+    # where the time went: submit -> copy seen done -> batch launched -> batch
+    # seen done -> curve ready, for the median request and the slowest 1 %
+    st = np.array([ecc.ecc_request_trace_us(h, rid) for rid in ids]) / 1e3
+    seg = np.diff(np.concatenate([np.zeros((len(st), 1)), st], axis=1), axis=1)
+    slow = lat >= np.percentile(lat, 99)
+    names = ["copy", "wait_launch", "batch", "complete"]
     vox = sum(int(np.prod(a.shape)) for a, _ in reqs)
     return {"requests": len(reqs), "rate_hz": rate_hz, "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
-            "gvox_s": vox / wall / 1e9, "wall_s": wall}
+            "gvox_s": vox / wall / 1e9, "wall_s": wall,
+            "stages_ms_median": {k: float(np.median(seg[:, i])) for i, k in enumerate(names)},
+            "stages_ms_slowest_1pct": {k: float(seg[slow, i].mean()) for i, k in enumerate(names)}}
 
 
 def config_volume14(steps: int, volume, h2d: dict):

@@ -245,7 +245,10 @@ int ecc_submit_borrowed(ecc_handle* h, const void* image, const int64_t* dims, i
                         ecc_dtype dtype, uint64_t* req_id);
 
 /* Waits up to timeout_us microseconds (0 = just check) for request req_id.
- * ECC_OK: *out holds the curve and the request is retired. ECC_PENDING: not
+ * ECC_OK: *out holds the curve and the request is retired (the curve of a
+ * batched request lies in place in a pinned result slab of the library,
+ * owned = 2, that of a streamed one in its own allocation, owned = 1; either
+ * is released by ecc_result_free). ECC_PENDING: not
  * done and timeout_us == 0. ECC_ERR_TIMEOUT: not done when the wait ran out.
  * ECC_ERR_ARG: unknown id. A failed request returns its error status once. */
 int ecc_poll(ecc_handle* h, uint64_t req_id, ecc_result* out, int64_t timeout_us);
@@ -253,6 +256,13 @@ int ecc_poll(ecc_handle* h, uint64_t req_id, ecc_result* out, int64_t timeout_us
 /* Latency record of a retired request, in microseconds from ecc_submit to the
  * completion event, for p50/p99 reporting. ECC_ERR_ARG if unknown. */
 int ecc_request_latency_us(ecc_handle* h, uint64_t req_id, double* us);
+
+/* Stages of a retired request, in microseconds from ecc_submit (-1 where a
+ * stage did not happen, e.g. a streamed request has no batch): stages[0] its
+ * device copy seen finished, [1] its batch launched, [2] its batch seen
+ * finished, [3] its curve ready (the latency). Instrumentation, no
+ * counterpart in the paper. ECC_ERR_ARG if unknown or not retired. */
+int ecc_request_trace_us(ecc_handle* h, uint64_t req_id, double* stages);
 
 /* Number of kernel launches this handle issued since it was created. */
 int64_t ecc_launch_count(const ecc_handle* h);

@@ -17,7 +17,9 @@
 // their device memory fits under the cap, launches the admitted ones as a
 // batch on one of two slots (two streams), and keeps launching new batches
 // while earlier ones run (continuous batching). Completion is detected by
-// events; results move to the request, device memory returns to the cap. A
+// events; a request's curve stays in place in the pinned slab its batch's
+// records were copied to (ecc_poll hands it out), device memory returns to
+// the cap. A
 // request larger than the ring is streamed through it in z-slabs on two
 // streams of its own, alongside the batches.
 #include "ecc_bits.cuh"
@@ -236,6 +238,15 @@ k_batch_bits(unsigned char* __restrict__ desc, DescLayout L) {
   if (cur >= 0) flush_bits_hist(imgs[cur], hist);
 }
 
+// Copies a batch's work list from the slot's pinned host buffer (mapped into
+// the device's address space) into device memory with the SMs, so that it
+// does not queue on the copy engine behind request images being uploaded.
+__global__ void __launch_bounds__(256)
+k_desc_pull(uint4* __restrict__ dst, const uint4* __restrict__ src, int64_t n16) {
+  for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n16; i += (int64_t)gridDim.x * 256)
+    dst[i] = src[i];
+}
+
 // Clears image blockIdx.x's VCEC (16-byte stores where it is 16-byte
 // aligned) and error word.
 __global__ void __launch_bounds__(kZeroThreads)
@@ -281,6 +292,7 @@ struct Slot {
   DescLayout L;
   DevBuf desc;
   unsigned char* h_desc = nullptr;
+  void* h_desc_dev = nullptr;  // h_desc as the device sees it (mapped pinned memory)
   DevBuf arena;
   unsigned char* h_arena = nullptr;
   size_t h_arena_cap = 0;
@@ -400,7 +412,8 @@ int slot_init(ecc_handle* h, Slot& sl, bool blocking) {
                                      blocking ? cudaStreamDefault : cudaStreamNonBlocking)) ||
       (e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming)) ||
       (e = cudaEventCreate(&sl.t0)) || (e = cudaEventCreate(&sl.t1)) ||
-      (e = sl.desc.ensure(sl.L.total)) || (e = cudaMallocHost(&sl.h_desc, sl.L.total)))
+      (e = sl.desc.ensure(sl.L.total)) || (e = cudaMallocHost(&sl.h_desc, sl.L.total)) ||
+      (e = cudaHostGetDevicePointer(&sl.h_desc_dev, sl.h_desc, 0)))
     return cuda_err(h, e, "batch slot");
   std::memset(sl.h_desc, 0, sl.L.total);
   return ECC_OK;
@@ -626,8 +639,14 @@ int slot_run(ecc_handle* h, Slot& sl, BatchTune& tune, const std::vector<ImgSpec
   hdr->n_chunks_b = nib > 0 ? n_chunks : 0;
   hdr->next_b = 0;
   if (wait_ev && (e = cudaStreamWaitEvent(sl.stream, wait_ev, 0))) return cuda_err(h, e, "wait");
-  if ((e = cudaMemcpyAsync(sl.desc.p, sl.h_desc, sl.L.total, cudaMemcpyHostToDevice, sl.stream)))
-    return cuda_err(h, e, "upload work list");
+  {
+    const int64_t n16 = (int64_t)(sl.L.total / 16);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(64, (n16 + 255) / 256));
+    k_desc_pull<<<blocks, 256, 0, sl.stream>>>(static_cast<uint4*>(sl.desc.p),
+                                               static_cast<const uint4*>(sl.h_desc_dev), n16);
+    ++h->launches;
+    if ((e = cudaGetLastError())) return cuda_err(h, e, "upload work list");
+  }
   cudaGraphExec_t& ex = large ? sl.exec_large : sl.exec_small;
   if (!ex) {
     e = h->cfg.convention == kConvT ? capture_graph<kConvT>(sl, large, &ex)
@@ -696,18 +715,20 @@ int64_t staged_pitch(const ecc_handle*, int dtype, int64_t, int64_t nx) {
 // Serving
 // ---------------------------------------------------------------------------
 
-// Pinned host memory that receives served batches' (curve, error word)
-// records: each batch takes one contiguous range, bump-allocated. live counts
-// the batches in flight plus the polled-for records in it (under the server
-// lock); a slab with nothing live starts over. So the request loop only reads
-// error words, and ecc_poll copies a curve out.
+// Pinned host memory that receives served batches' (header, curve, error
+// word) records: each batch takes one contiguous range, bump-allocated. The
+// memory is a refcounted ResultBlock: a finished request's curve stays in
+// place and ecc_poll hands it out (owned = 2), released by ecc_result_free.
+// live counts the batches in flight on the slab (under the server lock); a
+// slab with none in flight and no curve left (only the server's reference)
+// starts over.
 struct PinnedSlab {
-  unsigned char* p = nullptr;
-  size_t cap = 0;
+  ResultBlock* blk = nullptr;
   size_t used = 0;
   int live = 0;
 };
 constexpr size_t kSlabBytes = size_t(64) << 20;
+constexpr double kServeBatchVoxels = 256e6;
 
 struct Request {
   enum State { kQueuedHost, kOnDevice, kLaunched, kStreaming, kDone, kFailed, kRetired };
@@ -726,9 +747,11 @@ struct Request {
   int status = ECC_OK;
   int64_t* result = nullptr;
   int64_t result_bins = 0;
-  PinnedSlab* slab = nullptr;  // or: the curve sits in this slab at slab_off
-  size_t slab_off = 0;
+  long long* rec = nullptr;  // or: the curve in place in a result slab (one reference held)
   std::chrono::steady_clock::time_point t_submit, t_done;
+  // stages, for ecc_request_trace_us: device copy seen finished, batch
+  // launched, batch seen finished (unset: the epoch)
+  std::chrono::steady_clock::time_point t_copied, t_launched, t_retired;
   int slot = -1;
   // streamed requests (device copy larger than the ring): z-slab plan
   bool streamed = false;
@@ -763,10 +786,6 @@ struct Server {
   std::mutex mu;
   std::condition_variable cv;
   std::thread th;
-  // completion thread: copies finished batches' curves out of their slabs
-  std::thread done_th;
-  std::condition_variable done_cv;
-  std::deque<std::pair<std::vector<Request*>, PinnedSlab*>> done_q;
   bool stop = false;
   uint64_t next_id = 1;
   std::deque<Request*> queue;  // waiting for a launch, FIFO
@@ -786,6 +805,10 @@ struct Server {
   SlabJob* job = nullptr;
   cudaStream_t job_stream = nullptr, job_copy = nullptr;
   std::atomic<uint64_t> submitted{0};  // requests queued so far (wakes the poller)
+  // voxels per served batch at most: a burst of ready requests goes out as
+  // several batches on the two slots instead of one long one that every
+  // request in it waits for (ECC_SERVE_BATCH_VOXELS overrides)
+  double max_batch_vox = kServeBatchVoxels;
 };
 
 namespace {
@@ -835,6 +858,7 @@ bool copy_finished(Server* sv, Request* r) {
   if (q != cudaSuccess) cudaGetLastError();
   sv->ev_pool.push_back(r->copy_done);
   r->copy_done = nullptr;
+  r->t_copied = std::chrono::steady_clock::now();
   --sv->pending_copies;
   return true;
 }
@@ -850,13 +874,13 @@ void reap_copies(Server* sv) {
 }
 
 // A range of `need` bytes for one batch's records (caller holds mu): from the
-// current slab, else from a slab with nothing live, else null (the caller
+// current slab, else from a slab that can start over, else null (the caller
 // adds a slab). The batch holds one live count until it is retired.
 PinnedSlab* take_records(Server* sv, size_t need, size_t* off) {
   need = (need + 255) & ~size_t(255);
   auto try_slab = [&](PinnedSlab* sb) {
-    if (sb->live == 0) sb->used = 0;
-    if (sb->cap - sb->used < need) return false;
+    if (sb->live == 0 && sb->blk->refs.load(std::memory_order_acquire) == 1) sb->used = 0;
+    if (sb->blk->cap - sb->used < need) return false;
     *off = sb->used;
     sb->used += need;
     ++sb->live;
@@ -1158,36 +1182,6 @@ bool job_step(ecc_handle* h, Server* sv, std::unique_lock<std::mutex>& lk) {
   return progressed;
 }
 
-// Completion thread: each retired batch's curves out of its pinned slab into
-// the requests' own buffers, then the requests are done (ecc_poll returns
-// them) and their slab range is released. Runs beside the request loop, so
-// copying results does not hold up admissions and launches.
-void done_loop(Server* sv) {
-  std::unique_lock<std::mutex> lk(sv->mu);
-  while (true) {
-    sv->done_cv.wait(lk, [&] { return sv->stop || !sv->done_q.empty(); });
-    if (sv->stop) break;
-    auto item = std::move(sv->done_q.front());
-    sv->done_q.pop_front();
-    lk.unlock();
-    for (Request* r : item.first) {
-      const int64_t bins = r->result_bins;
-      r->result = static_cast<int64_t*>(std::malloc(sizeof(int64_t) * std::max<int64_t>(bins, 1)));
-      if (r->result) std::memcpy(r->result, r->slab->p + r->slab_off, sizeof(int64_t) * bins);
-      else r->status = ECC_ERR_OOM;
-    }
-    const auto now = std::chrono::steady_clock::now();
-    lk.lock();
-    for (Request* r : item.first) {
-      r->slab = nullptr;
-      r->state = r->status == ECC_OK ? Request::kDone : Request::kFailed;
-      r->t_done = now;
-    }
-    item.second->live -= (int)item.first.size();
-    sv->cv.notify_all();
-  }
-}
-
 void serve_loop(ecc_handle* h) {
   Server* sv = h->server;
   cudaSetDevice(h->device);
@@ -1209,20 +1203,24 @@ void serve_loop(ecc_handle* h) {
       const size_t base = sv->slot_res[s].second;
       sv->slot_res[s] = {nullptr, 0};
       lk.unlock();
-      int held = 0;  // records that stay in the slab until polled
+      // statuses from the error words; a finished curve stays where the copy
+      // back put it, its header naming the slab's block, and the request holds
+      // a reference until ecc_poll hands it out
       for (size_t i = 0; i < fl.size(); ++i) {
         Request* r = fl[i];
         if (q != cudaSuccess) {
           r->status = ECC_ERR_CUDA;
           continue;
         }
-        const size_t off = base + sv->eng.slots[s].res_off[i];
-        r->status = record_status(reinterpret_cast<const long long*>(sb->p + off), r->bins);
+        long long* rec = reinterpret_cast<long long*>(sb->blk->p + base + sv->eng.slots[s].res_off[i]);
+        r->status = record_status(rec, r->bins);
         if (r->status == ECC_OK) {
-          r->slab = sb;
-          r->slab_off = off;
+          uint64_t* hdr = reinterpret_cast<uint64_t*>(rec) - 2;
+          hdr[0] = reinterpret_cast<uint64_t>(sb->blk);
+          hdr[1] = kResultMagic;
+          sb->blk->refs.fetch_add(1, std::memory_order_relaxed);
+          r->rec = rec;
           r->result_bins = r->bins;
-          ++held;
         }
       }
       if (q != cudaSuccess) cudaGetLastError();
@@ -1232,26 +1230,15 @@ void serve_loop(ecc_handle* h) {
       for (Request* r : fl)
         if (r->d_img) cudaFreeAsync(r->d_img, sv->eng.slots[s].stream);
       lk.lock();
-      // failed requests finish here; the others when the completion thread
-      // has copied their curves (the slab range is held until then)
-      sb->live += held - 1;
-      std::vector<Request*> ok;
-      ok.reserve(held);
+      --sb->live;
       for (Request* r : fl) {
         if (r->d_img) {
           r->d_img = nullptr;
           sv->bytes_in_use -= request_cost(r);
         }
-        if (r->status == ECC_OK) {
-          ok.push_back(r);
-        } else {
-          r->state = Request::kFailed;
-          r->t_done = now;
-        }
-      }
-      if (!ok.empty()) {
-        sv->done_q.emplace_back(std::move(ok), sb);
-        sv->done_cv.notify_one();
+        r->t_retired = now;
+        r->t_done = now;
+        r->state = r->status == ECC_OK ? Request::kDone : Request::kFailed;
       }
       progressed = true;
     }
@@ -1298,6 +1285,7 @@ void serve_loop(ecc_handle* h) {
       std::vector<ImgSpec> specs;
       bool in_flight_seen = false;
       size_t rec_bytes = 0;  // the batch's result records fit one slab
+      double batch_vox = 0;  // and its voxels stay under the cap (the first request always goes)
       for (auto it = sv->queue.begin(); it != sv->queue.end() && (int)batch.size() < kMaxBatch;) {
         Request* r = *it;
         if (r->state == Request::kFailed) {
@@ -1310,9 +1298,12 @@ void serve_loop(ecc_handle* h) {
           ++it;
           continue;
         }
-        const size_t rb = sizeof(long long) * (r->bins + 1);
-        if (!batch.empty() && rec_bytes + rb > kSlabBytes) break;
+        const size_t rb = kResultHeader + sizeof(long long) * (r->bins + 1);
+        const double rv = (double)r->n[0] * (double)r->n[1] * (double)r->n[2];
+        if (!batch.empty() && (rec_bytes + rb > kSlabBytes || batch_vox + rv > sv->max_batch_vox))
+          break;
         rec_bytes += rb;
+        batch_vox += rv;
         batch.push_back(r);
         specs.push_back(
             ImgSpec{r->d_img, {r->n[0], r->n[1], r->n[2]}, r->dtype, r->bins, r->pitch});
@@ -1337,9 +1328,11 @@ void serve_loop(ecc_handle* h) {
         PinnedSlab* fresh = nullptr;
         if (!sb) {
           fresh = new PinnedSlab();
-          fresh->cap = std::max(kSlabBytes, (need + 255) & ~size_t(255));
-          if (cudaMallocHost(&fresh->p, fresh->cap) != cudaSuccess) {
+          fresh->blk = new ResultBlock();
+          fresh->blk->cap = std::max(kSlabBytes, (need + 255) & ~size_t(255));
+          if (cudaMallocHost(&fresh->blk->p, fresh->blk->cap) != cudaSuccess) {
             cudaGetLastError();
+            delete fresh->blk;
             delete fresh;
             fresh = nullptr;
             rc = set_err(h, ECC_ERR_OOM, "pinned result slab");
@@ -1350,7 +1343,7 @@ void serve_loop(ecc_handle* h) {
           sv->slabs.push_back(fresh);
           sb = take_records(sv, need, &off);  // fits: the new slab is empty
         }
-        if (!rc) rc = slot_run(h, sl, sv->eng.tune, sv->specs[free_slot], nullptr, sb->p + off);
+        if (!rc) rc = slot_run(h, sl, sv->eng.tune, sv->specs[free_slot], nullptr, sb->blk->p + off);
         lk.lock();
         if (rc) {
           if (sb) --sb->live;
@@ -1361,6 +1354,8 @@ void serve_loop(ecc_handle* h) {
             free_device_image(sv, r);
           }
         } else {
+          const auto now = std::chrono::steady_clock::now();
+          for (Request* r : batch) r->t_launched = now;
           sv->in_flight[free_slot] = std::move(batch);
           sv->slot_res[free_slot] = {sb, off};
         }
@@ -1415,6 +1410,10 @@ int server_start(ecc_handle* h) {
       return rc;
     }
   }
+  if (const char* v = std::getenv("ECC_SERVE_BATCH_VOXELS")) {
+    const double x = std::atof(v);
+    if (x > 0) sv->max_batch_vox = x;
+  }
   sv->in_flight.resize(2);
   sv->specs.resize(2);
   sv->slot_res.assign(2, {nullptr, 0});
@@ -1426,7 +1425,6 @@ int server_start(ecc_handle* h) {
   }
   h->server = sv;
   sv->th = std::thread(serve_loop, h);
-  sv->done_th = std::thread(done_loop, sv);
   return ECC_OK;
 }
 
@@ -1440,9 +1438,7 @@ void serve_shutdown(ecc_handle* h) {
       sv->stop = true;
     }
     sv->cv.notify_all();
-    sv->done_cv.notify_all();
     if (sv->th.joinable()) sv->th.join();
-    if (sv->done_th.joinable()) sv->done_th.join();
     cudaSetDevice(h->device);
     for (Slot& sl : sv->eng.slots) slot_free(sl);
     if (sv->job) job_release(sv, sv->job);
@@ -1452,12 +1448,14 @@ void serve_shutdown(ecc_handle* h) {
       if (r->d_img) cudaFreeAsync(r->d_img, sv->copy_stream);
       if (r->copy_done) cudaEventDestroy(r->copy_done);
       std::free(r->result);
+      if (r->rec) result_block_release(
+          reinterpret_cast<ResultBlock*>(reinterpret_cast<const uint64_t*>(r->rec)[-2]));
       delete r;
     }
     cudaStreamSynchronize(sv->copy_stream);
     for (cudaEvent_t e : sv->ev_pool) cudaEventDestroy(e);
     for (PinnedSlab* sb : sv->slabs) {
-      cudaFreeHost(sb->p);
+      result_block_release(sb->blk);  // freed now, or with the last result handed out
       delete sb;
     }
     cudaStreamDestroy(sv->copy_stream);
@@ -1777,6 +1775,7 @@ static int submit_request(ecc_handle* h, const void* image, const int64_t* dims,
     }
     if (copied) {
       const int rc = wait_event(h, copied, 300LL * 1000 * 1000);
+      r->t_copied = std::chrono::steady_clock::now();
       std::lock_guard<std::mutex> lk(sv->mu);
       sv->ev_pool.push_back(copied);
       if (rc) {
@@ -1850,12 +1849,36 @@ int ecc_poll(ecc_handle* h, uint64_t req_id, ecc_result* out, int64_t timeout_us
   const int rc = r->status;
   r->state = Request::kRetired;
   if (rc == ECC_OK) {
-    out->owned = 1;
     out->bins = r->result_bins;
-    out->curve = r->result;
-    r->result = nullptr;
+    if (r->rec) {
+      out->owned = 2;  // in place in a result slab; the request's reference moves to out
+      out->curve = reinterpret_cast<int64_t*>(r->rec);
+      r->rec = nullptr;
+    } else {
+      out->owned = 1;
+      out->curve = r->result;
+      r->result = nullptr;
+    }
   }
   return rc;
+}
+
+int ecc_request_trace_us(ecc_handle* h, uint64_t req_id, double* stages) {
+  if (!h || !stages || !h->server) return ECC_ERR_ARG;
+  Server* sv = h->server;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->all.find(req_id);
+  if (it == sv->all.end()) return ECC_ERR_ARG;
+  Request* r = it->second;
+  if (r->state != Request::kDone && r->state != Request::kRetired && r->state != Request::kFailed)
+    return ECC_ERR_ARG;
+  const std::chrono::steady_clock::time_point ts[4] = {r->t_copied, r->t_launched, r->t_retired,
+                                                       r->t_done};
+  for (int k = 0; k < 4; ++k)
+    stages[k] = ts[k].time_since_epoch().count() == 0
+                    ? -1.0
+                    : std::chrono::duration<double, std::micro>(ts[k] - r->t_submit).count();
+  return ECC_OK;
 }
 
 int ecc_request_latency_us(ecc_handle* h, uint64_t req_id, double* us) {

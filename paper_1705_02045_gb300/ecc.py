@@ -72,6 +72,7 @@ _SIGNATURES = {
     "ecc_submit_borrowed": (C.c_int, [_P, _P, _I64P, C.c_int, C.c_int, C.POINTER(C.c_uint64)]),
     "ecc_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(ecc_result), C.c_int64]),
     "ecc_request_latency_us": (C.c_int, [_P, C.c_uint64, C.POINTER(C.c_double)]),
+    "ecc_request_trace_us": (C.c_int, [_P, C.c_uint64, C.POINTER(C.c_double)]),
     "ecc_launch_count": (C.c_int64, [_P]),
     "ecc_set_profiling": (C.c_int, [_P, C.c_int]),
     "ecc_profile_read": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
@@ -388,6 +389,14 @@ def ecc_request_latency_us(h, req_id: int) -> float:
     v = C.c_double()
     _check(h, load().ecc_request_latency_us(h, C.c_uint64(req_id), C.byref(v)))
     return v.value
+
+
+def ecc_request_trace_us(h, req_id: int):
+    """(copied, launched, batch finished, done) microseconds after submit; -1
+    for a stage that did not happen."""
+    st = (C.c_double * 4)()
+    _check(h, load().ecc_request_trace_us(h, C.c_uint64(req_id), st))
+    return tuple(st)
 
 
 def ecc_launch_count(h) -> int:

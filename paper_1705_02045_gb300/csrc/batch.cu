@@ -656,17 +656,17 @@ int slot_run(ecc_handle* h, Slot& sl, BatchTune& tune, const std::vector<ImgSpec
   // instrumentation (profile): an event pair of the handle's profiling record
   // around the graph
   cudaEvent_t pa = nullptr, pb = nullptr;
-  if (profile && (cudaEventCreate(&pa) != cudaSuccess || cudaEventCreate(&pb) != cudaSuccess)) {
-    if (pa) cudaEventDestroy(pa);
-    if (pb) cudaEventDestroy(pb);
+  if (profile && (prof_event_take(h, &pa) != cudaSuccess || prof_event_take(h, &pb) != cudaSuccess)) {
+    prof_event_give(h, pa);
+    prof_event_give(h, pb);
     pa = pb = nullptr;
     cudaGetLastError();
   }
   if ((e = cudaEventRecord(sl.t0, sl.stream)) || (pa && (e = cudaEventRecord(pa, sl.stream))) ||
       (e = cudaGraphLaunch(ex, sl.stream)) || (pb && (e = cudaEventRecord(pb, sl.stream))) ||
       (e = cudaEventRecord(sl.t1, sl.stream))) {
-    if (pa) cudaEventDestroy(pa);
-    if (pb) cudaEventDestroy(pb);
+    prof_event_give(h, pa);
+    prof_event_give(h, pb);
     return cuda_err(h, e, "graph launch");
   }
   if (pa) h->prof_events.emplace_back(pa, pb);

@@ -159,6 +159,19 @@ constexpr size_t kUploadTailBytes = size_t(2) << 20;
 // little work left once the copy has ended). ends[k] is the first plane after
 // chunk k, whose arrival h->up_ev[k] marks. The copies wait for the buffer's
 // earlier readers (kernels on the compute stream).
+cudaError_t prof_event_take(ecc_handle* h, cudaEvent_t* ev) {
+  if (!h->prof_pool.empty()) {
+    *ev = h->prof_pool.back();
+    h->prof_pool.pop_back();
+    return cudaSuccess;
+  }
+  return cudaEventCreate(ev);
+}
+
+void prof_event_give(ecc_handle* h, cudaEvent_t ev) {
+  if (ev) h->prof_pool.push_back(ev);
+}
+
 void result_block_release(ResultBlock* b) {
   if (b && b->refs.fetch_sub(1, std::memory_order_acq_rel) == 1) {
     cudaFreeHost(b->p);
@@ -275,17 +288,18 @@ int enqueue_int(ecc_handle* h, const void* d_img, int64_t row_pitch, const Shape
       a.fused_curve = d_curve;
       a.done = h->done.as<unsigned int>();
     }
-    // profiling events: destroyed on every return that does not hand them
-    // to the handle's record
+    // profiling events: back to the pool on every return that does not hand
+    // them to the handle's record
     struct EventPair {
+      ecc_handle* h;
       cudaEvent_t a = nullptr, b = nullptr;
       ~EventPair() {
-        if (a) cudaEventDestroy(a);
-        if (b) cudaEventDestroy(b);
+        prof_event_give(h, a);
+        prof_event_give(h, b);
       }
-    } prof;
+    } prof{h};
     if (h->prof_on) {
-      if ((e = cudaEventCreate(&prof.a)) || (e = cudaEventCreate(&prof.b)) ||
+      if ((e = prof_event_take(h, &prof.a)) || (e = prof_event_take(h, &prof.b)) ||
           (e = cudaEventRecord(prof.a, stream)))
         return cuda_err(h, e, "profiling event");
     }
@@ -408,9 +422,10 @@ static int compute_float(ecc_handle* h, const void* d_img, const Shape& s, ecc_r
   a.stream = st;
   cudaEvent_t pa = nullptr, pb = nullptr;  // profiling: events around the pairs kernel
   if (h->prof_on) {
-    if ((e = cudaEventCreate(&pa)) || (e = cudaEventCreate(&pb)) || (e = cudaEventRecord(pa, st))) {
-      if (pa) cudaEventDestroy(pa);
-      if (pb) cudaEventDestroy(pb);
+    if ((e = prof_event_take(h, &pa)) || (e = prof_event_take(h, &pb)) ||
+        (e = cudaEventRecord(pa, st))) {
+      prof_event_give(h, pa);
+      prof_event_give(h, pb);
       return cuda_err(h, e, "profiling event");
     }
   }
@@ -425,8 +440,8 @@ static int compute_float(ecc_handle* h, const void* d_img, const Shape& s, ecc_r
   if (pa && e == cudaSuccess && (e = cudaEventRecord(pb, st)) == cudaSuccess) {
     h->prof_events.emplace_back(pa, pb);
   } else if (pa) {
-    cudaEventDestroy(pa);
-    cudaEventDestroy(pb);
+    prof_event_give(h, pa);
+    prof_event_give(h, pb);
   }
   if (e) return cuda_err(h, e, "pairs kernel");
   h->launches += cnt;
@@ -567,6 +582,7 @@ void ecc_destroy(ecc_handle* h) {
     cudaEventDestroy(pr.first);
     cudaEventDestroy(pr.second);
   }
+  for (cudaEvent_t ev : h->prof_pool) cudaEventDestroy(ev);
   delete h->tuner;
   if (h->h_err) cudaFreeHost(h->h_err);
   if (h->h_curve) cudaFreeHost(h->h_curve);
@@ -865,8 +881,8 @@ int ecc_profile_read(ecc_handle* h, double* contrib_ms, int64_t* count) {
     hi = i == 0 ? b : std::max(hi, (double)b);
   }
   for (auto& pr : h->prof_events) {
-    cudaEventDestroy(pr.first);
-    cudaEventDestroy(pr.second);
+    prof_event_give(h, pr.first);
+    prof_event_give(h, pr.second);
   }
   *count = (int64_t)h->prof_events.size();
   h->prof_events.clear();

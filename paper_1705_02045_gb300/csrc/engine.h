@@ -121,6 +121,7 @@ struct ecc_handle {
   bool prof_on = false;
   double prof_span_ms = 0.0;           // span of the record read last (ecc_profile_span)
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
+  std::vector<cudaEvent_t> prof_pool;  // events of earlier records, for reuse
 
   // batched launches and serving (batch.cu)
   ecc::BatchEngine* batch = nullptr;   // used by ecc_compute_batch
@@ -169,6 +170,10 @@ cudaError_t launch_local(const LocalArgs& a, int num_sms, int64_t* launches);
 // shared-memory histogram from overflowing.
 int64_t max_planes_per_launch(const Shape& s, int num_sms);
 void serve_shutdown(ecc_handle* h);
+// Profiling events from the handle's pool (creating events costs host time
+// on every call): take one, or give one back (caller holds api_mu).
+cudaError_t prof_event_take(ecc_handle* h, cudaEvent_t* ev);
+void prof_event_give(ecc_handle* h, cudaEvent_t ev);
 // Times candidate launch shapes of the bit-sliced kernel on this launch.
 int tune_bits(ecc_handle* h, const LocalArgs& base, TuneChoice* best);
 int bits_nb(int dtype, int64_t bins);

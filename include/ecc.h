@@ -149,6 +149,24 @@ int ecc_compute_device(ecc_handle* h, const void* d_image, const int64_t* dims,
                        int ndim, ecc_dtype dtype, int64_t bins,
                        int64_t* d_curve, void* stream);
 
+/* Partial VCEC of one chunk of an integer image, for computations that cut
+ * an image along dims[0] and combine the parts elsewhere (Sec. 3, "Parallel
+ * Computations": each chunk's VCEC is computed on its own and the VCECs are
+ * summed in "Post-Processing"; Sec. 6 notes the method fits map-reduce).
+ * vcec[t], t < bins (the handle's default bins for dtype), receives the sum
+ * of the changes of Algorithm 1 of the voxels in planes [z_lo, z_hi) of the
+ * image at value t: summed over any partition of [0, dims[0]) they give the
+ * image's VCEC, whose prefix sum is the curve. dims: the whole image's
+ * dimensions (1-4D). planes: host or device memory holding planes
+ * [max(z_lo - 1, 0), min(z_hi + 1, dims[0])) of the image, C order: the chunk
+ * and the one-plane collar on each side where the image has one (a device
+ * pointer aligned to its element size). vcec: host int64[bins], written.
+ * Blocks until done. Errors: ECC_ERR_ARG (z range outside 0..dims[0], null
+ * pointers), ECC_ERR_DTYPE, ECC_ERR_VALUE (a value >= bins), ECC_ERR_OOM,
+ * ECC_ERR_CUDA. */
+int ecc_compute_vcec_chunk(ecc_handle* h, const void* planes, const int64_t* dims, int ndim,
+                           ecc_dtype dtype, int64_t z_lo, int64_t z_hi, int64_t* vcec);
+
 /* ECC of a float32 image through the value transform of Sec. 3 ("Other
  * Ranges of Gray Values": shift, scale and round the values into 0..m-1, then
  * run the integer algorithm): code(v) = clamp(floor((v - lo) * s), 0, bins-1)

@@ -831,6 +831,89 @@ int ecc_compute_quantized(ecc_handle* h, const float* image, const int64_t* dims
   }
 }
 
+int ecc_compute_vcec_chunk(ecc_handle* h, const void* planes, const int64_t* dims, int ndim,
+                           ecc_dtype dtype, int64_t z_lo, int64_t z_hi, int64_t* vcec) {
+  if (!h) return ECC_ERR_ARG;
+  try {
+    std::lock_guard<std::mutex> lk(h->api_mu);
+    clear_err(h);
+    Shape s;
+    int rc = validate_shape(h, dims, ndim, &s);
+    if (rc) return rc;
+    if (dtype != ECC_U8 && dtype != ECC_U16)
+      return set_err(h, ECC_ERR_DTYPE, "ecc_compute_vcec_chunk takes ECC_U8 or ECC_U16");
+    if (!vcec) return set_err(h, ECC_ERR_ARG, "vcec is NULL");
+    if (ndim < 3) {
+      // march along dims[0]: a 1D or 2D image viewed as (dims[0], 1, nx), which
+      // embeds the same complex with the same linear order as (1, ny, nx)
+      s.n[0] = dims[0];
+      s.n[1] = 1;
+      s.n[2] = ndim == 2 ? dims[1] : 1;
+    }
+    const int64_t n0 = s.n[0];
+    if (z_lo < 0 || z_hi > n0 || z_lo > z_hi)
+      return set_err(h, ECC_ERR_ARG, "need 0 <= z_lo <= z_hi <= dims[0]");
+    const int64_t bins = default_bins(h, dtype);
+    // the chunk and its one-plane collars, where the image has them
+    const int64_t p_lo = std::max<int64_t>(z_lo - 1, 0), p_hi = std::min<int64_t>(z_hi + 1, n0);
+    const int64_t plane = s.voxels / std::max<int64_t>(n0, 1);
+    const size_t bytes = dtype_bytes(dtype) * (size_t)(plane * (p_hi - p_lo));
+    if (bytes > 0 && !planes) return set_err(h, ECC_ERR_ARG, "planes is NULL");
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e) return cuda_err(h, e, "set device");
+    if ((e = h->vcec.ensure(sizeof(long long) * bins))) return cuda_err(h, e, "vcec buffer");
+    cudaStream_t st = h->stream;
+    if ((e = cudaMemsetAsync(h->vcec.p, 0, sizeof(long long) * bins, st)) ||
+        (e = cudaMemsetAsync(h->errw.p, 0, sizeof(int), st)))
+      return cuda_err(h, e, "memset");
+    h->clean_vcec = nullptr;  // this call leaves the VCEC filled
+    const void* d_planes = planes;
+    if (bytes > 0 && !is_device_ptr(h, planes)) {
+      if ((e = h->img.ensure(bytes))) return cuda_err(h, e, "image buffer");
+      if ((e = cudaMemcpyAsync(h->img.p, planes, bytes, cudaMemcpyHostToDevice, st)))
+        return cuda_err(h, e, "copy planes");
+      d_planes = h->img.p;
+    } else if (bytes > 0 && !elem_aligned(planes, dtype)) {
+      return set_err(h, ECC_ERR_ARG, "device planes not aligned to their element size");
+    }
+    if (z_hi > z_lo && s.voxels > 0) {
+      LocalArgs a;
+      a.img = d_planes;
+      a.dtype = dtype;
+      a.conv = h->cfg.convention;
+      a.view = s.view;
+      for (int i = 0; i < 4; ++i) a.n[i] = s.n[i];
+      a.bins = bins;
+      a.variant = h->variant;
+      a.warps = h->bits_warps;
+      a.zc = h->bits_zc;
+      a.layout = h->bits_layout;
+      a.vcec = h->vcec.as<long long>();
+      a.err = h->errw.as<int>();
+      a.stream = st;
+      a.w_mem_lo = p_lo;
+      a.w_mem_hi = p_hi;
+      const int64_t step = max_planes_per_launch(s, h->num_sms);
+      for (int64_t w = z_lo; w < z_hi; w += step) {
+        a.w_lo = w;
+        a.w_hi = std::min(z_hi, w + step);
+        int64_t cnt = 0;
+        e = launch_local(a, h->num_sms, &cnt);
+        h->launches += cnt;
+        if (e != cudaSuccess) return cuda_err(h, e, "contribution kernel");
+      }
+    }
+    if ((e = cudaMemcpyAsync(vcec, h->vcec.p, sizeof(long long) * bins, cudaMemcpyDeviceToHost,
+                             st)))
+      return cuda_err(h, e, "copy vcec");
+    int word = 0;
+    if ((rc = read_err_word(h, st, &word))) return rc;
+    return err_word_status(h, word);
+  } catch (...) {
+    return set_err(h, ECC_ERR_CUDA, "internal error");
+  }
+}
+
 int ecc_device_status(ecc_handle* h) {
   if (!h) return ECC_ERR_ARG;
   try {

@@ -59,6 +59,8 @@ _SIGNATURES = {
     "ecc_compute": (C.c_int, [_P, _P, _I64P, C.c_int, C.c_int, C.POINTER(ecc_result)]),
     "ecc_compute_device": (C.c_int, [_P, _P, _I64P, C.c_int, C.c_int, C.c_int64, _P, _P]),
     "ecc_device_status": (C.c_int, [_P]),
+    "ecc_compute_vcec_chunk": (C.c_int, [_P, _P, _I64P, C.c_int, C.c_int, C.c_int64, C.c_int64,
+                                         _I64P]),
     "ecc_compute_quantized": (C.c_int, [_P, _P, _I64P, C.c_int, C.c_float, C.c_float, C.c_int64,
                                         C.POINTER(ecc_result)]),
     "ecc_stream_begin": (C.c_int, [_P, _I64P, C.c_int, C.c_int, C.POINTER(_P)]),
@@ -264,6 +266,19 @@ def ecc_compute_device(h, d_image, bins: int, d_curve, stream=None) -> None:
     _check(h, lib.ecc_compute_device(h, C.c_void_p(d_image.data_ptr()), dims,
                                      len(d_image.shape), _dtype_code(d_image.dtype),
                                      int(bins), C.c_void_p(d_curve.data_ptr()), st))
+
+
+def ecc_compute_vcec_chunk(h, planes, shape, z_lo: int, z_hi: int, bins: int):
+    """Partial VCEC (int64[bins]) of planes [z_lo, z_hi) of an integer image of
+    `shape`; `planes` holds planes [max(z_lo-1, 0), min(z_hi+1, shape[0]))
+    (numpy or torch, host or CUDA)."""
+    ptr, keep = _data_ptr(planes)
+    out = np.zeros(int(bins), dtype=np.int64)
+    _check(h, load().ecc_compute_vcec_chunk(h, ptr, _dims(shape), len(shape),
+                                            _dtype_code(planes.dtype), int(z_lo), int(z_hi),
+                                            out.ctypes.data_as(_I64P)))
+    del keep
+    return out
 
 
 def ecc_device_status(h) -> int:

@@ -1,0 +1,529 @@
+// Bit-sliced contribution kernel for 4D images (integer values or float32
+// keys), marching along the slowest axis w.
+//
+// The quantity is that of Algorithm 1 (Sec. 3): per voxel the signed count of
+// the faces it introduces, at its gray value. As in the 3D bit-sliced kernels
+// a lane holds 32 voxels of one row as bit planes (float32 values as their
+// order-preserving 32-bit keys, 32 planes), each unordered neighbour pair is
+// compared once by a borrow chain, and voxels outside the image count as +inf
+// (the infinite collar of Sec. 4) through outside masks. In 4D a voxel has 80
+// neighbours: 40 later in the linear order, 13 of them in its own volume w
+// and 27 in volume w + 1. The change is evaluated through the factorisation
+// along w,
+//     G_4(M) = G_3(m0) - b+ G_3(m0 & m+) - b- G_3(m0 & m-),
+// with m0 the 26 after-bits in the own volume, m+- those of volumes w +- 1 at
+// the same 3D offsets and b+- the straight w neighbours; each G_3 is 13 - N
+// with N the 26-term count of the 3D kernels.
+//
+// Layout: a block of 8 warps holds 8 consecutive z-slices of one 30 x 30
+// (y, x) tile (warps 0 and 7 are the z-collar, the 6 between own slices);
+// a warp holds 32 rows of its slice (lanes 0 and 31 the y-collar) and a lane
+// one 32-voxel word (bits 0 and 31 the x-collar), as in the warp-column
+// layout of the 3D kernel. The block marches along w; each lane keeps its
+// row's planes of volumes w and w + 1 in registers, the neighbouring slices'
+// planes come through shared memory (double-buffered by volume parity), rows
+// y +- 1 of a slice by warp shuffles. Comparison words travel to the later
+// voxel's row through shared memory: those with slice z + 1 within the step,
+// those with volume w + 1 to the next step. Two block barriers per step.
+#pragma once
+
+#include "ecc_bitsw.cuh"
+#include "ecc_device.cuh"
+
+namespace ecc {
+
+constexpr int k4ZB = 6;             // own z-slices per block
+constexpr int k4Warps = k4ZB + 2;   // one warp per slice, the two collar slices included
+
+struct Bits4Img {
+  const unsigned char* img;  // volume w_mem_lo
+  int64_t n[4];              // w, z, y, x
+  int64_t w_mem_lo, w_mem_hi;
+  int64_t bins;
+  long long* vcec;
+  int* err;
+  unsigned long long* pairs;  // float images: (key << 32 | change)
+  unsigned long long* pair_count;
+  int64_t pair_cap;
+};
+
+struct Bits4Geo {
+  int64_t tiles_x, tiles_y, tiles_z, cols;
+};
+
+inline Bits4Geo bits4_geo(int64_t nz, int64_t ny, int64_t nx) {
+  Bits4Geo g{};
+  g.tiles_x = (nx + kWcOwn - 1) / kWcOwn;
+  g.tiles_y = (ny + kWcOwn - 1) / kWcOwn;
+  g.tiles_z = (nz + k4ZB - 1) / k4ZB;
+  g.cols = g.tiles_x * g.tiles_y * g.tiles_z;
+  return g;
+}
+
+// Shared-memory words of one block: planes of both volumes for every slice,
+// the in-volume exports to slice z + 1, the cross exports of two steps.
+template <int NB>
+constexpr size_t bits4_smem_words() {
+  return (size_t)2 * k4Warps * NB * 32 + (size_t)k4Warps * 9 * 32 + (size_t)2 * k4Warps * 27 * 32;
+}
+
+namespace b4 {
+
+// 32 x 32 bit transpose by five delta swaps: afterwards A[k] bit j = bit k of
+// the original A[j].
+__device__ __forceinline__ void transpose32(uint32_t A[32]) {
+  const uint32_t M[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const int s = 16 >> st;
+    const uint32_t m = M[st];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (j & s) continue;
+      const uint32_t a = A[j], b = A[j | s];
+      const uint32_t t = ((a >> s) ^ b) & m;
+      A[j] = a ^ (t << s);
+      A[j | s] = b ^ t;
+    }
+  }
+}
+
+// Words [0, 32) of the 32 float32 values starting at voxel x0 (may be -1) of
+// a row; voxels outside [0, nx) read as 0. fast: the row starts on a 16-byte
+// boundary (16-byte loads; the in-chunk offset is the same in every lane).
+__device__ __forceinline__ void load_window4(const unsigned char* row, int64_t x0, int64_t nx,
+                                             bool fast, uint32_t* raw) {
+  const int64_t vb0 = (x0 < 0 ? 0 : x0) * 4, vb1 = (x0 + 32 < nx ? x0 + 32 : nx) * 4;
+  const int64_t s = x0 * 4;
+  if (fast) {
+    const int64_t a = s & ~int64_t(15);
+    const int q = (int)((s - a) >> 2);
+    uint32_t w[36];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      const int64_t cb = a + 16 * c;
+      if (cb + 16 > vb0 && cb < vb1) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(row + cb));
+        w[4 * c] = v.x;
+        w[4 * c + 1] = v.y;
+        w[4 * c + 2] = v.z;
+        w[4 * c + 3] = v.w;
+      } else {
+        w[4 * c] = w[4 * c + 1] = w[4 * c + 2] = w[4 * c + 3] = 0u;
+      }
+    }
+    // the window's first element is word q of the chunks: one of four unrolled
+    // selections
+    switch (q) {
+#define ECC_B4_SELECT(Q)                                                  \
+  case Q:                                                                 \
+    _Pragma("unroll") for (int i = 0; i < 32; ++i) raw[i] = w[i + Q];     \
+    break;
+      ECC_B4_SELECT(0)
+      ECC_B4_SELECT(1)
+      ECC_B4_SELECT(2)
+      ECC_B4_SELECT(3)
+#undef ECC_B4_SELECT
+    }
+  } else {
+    // element-aligned words
+    const uint32_t* p = reinterpret_cast<const uint32_t*>(row);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const int64_t x = x0 + i;
+      raw[i] = (x >= 0 && x < nx) ? __ldg(p + x) : 0u;
+    }
+  }
+}
+
+// Bit-sliced 26-term count of the 3D kernels over the neighbour words
+// w[dz+1][dy+1][dx+1] (centre unused): faces, complemented edge triples and
+// vertex 7-boxes; G_3(w) = 13 - N. n[0..4]: the bit planes of N.
+__device__ __forceinline__ void count26(const uint32_t (&w)[3][3][3], uint32_t n[5]) {
+  using namespace bits;
+  auto W = [&](int dz, int dy, int dx) -> uint32_t { return w[dz + 1][dy + 1][dx + 1]; };
+  uint32_t tm[26];
+  int t = 0;
+  tm[t++] = W(0, 0, 1);
+  tm[t++] = W(0, 0, -1);
+  tm[t++] = W(0, 1, 0);
+  tm[t++] = W(0, -1, 0);
+  tm[t++] = W(1, 0, 0);
+  tm[t++] = W(-1, 0, 0);
+  uint32_t Exy[2][2];
+#pragma unroll
+  for (int sx = 0; sx < 2; ++sx)
+#pragma unroll
+    for (int sy = 0; sy < 2; ++sy) {
+      const int dx = sx ? 1 : -1, dy = sy ? 1 : -1;
+      Exy[sx][sy] = W(0, 0, dx) & W(0, dy, 0) & W(0, dy, dx);
+      tm[t++] = ~Exy[sx][sy];
+    }
+#pragma unroll
+  for (int sx = 0; sx < 2; ++sx)
+#pragma unroll
+    for (int sz = 0; sz < 2; ++sz) {
+      const int dx = sx ? 1 : -1, dz = sz ? 1 : -1;
+      tm[t++] = ~(W(0, 0, dx) & W(dz, 0, 0) & W(dz, 0, dx));
+    }
+#pragma unroll
+  for (int sy = 0; sy < 2; ++sy)
+#pragma unroll
+    for (int sz = 0; sz < 2; ++sz) {
+      const int dy = sy ? 1 : -1, dz = sz ? 1 : -1;
+      tm[t++] = ~(W(0, dy, 0) & W(dz, 0, 0) & W(dz, dy, 0));
+    }
+#pragma unroll
+  for (int sx = 0; sx < 2; ++sx)
+#pragma unroll
+    for (int sy = 0; sy < 2; ++sy)
+#pragma unroll
+      for (int sz = 0; sz < 2; ++sz) {
+        const int dx = sx ? 1 : -1, dy = sy ? 1 : -1, dz = sz ? 1 : -1;
+        tm[t++] = Exy[sx][sy] & W(dz, 0, 0) & W(dz, 0, dx) & W(dz, dy, 0) & W(dz, dy, dx);
+      }
+  uint32_t s[8], c[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) fa(tm[3 * i], tm[3 * i + 1], tm[3 * i + 2], s[i], c[i]);
+  uint32_t a0, a1, a2, d0, d1, d2, b0, e0, e1;
+  fa(s[0], s[1], s[2], a0, d0);
+  fa(s[3], s[4], s[5], a1, d1);
+  fa(s[6], s[7], tm[24], a2, d2);
+  fa(a0, a1, a2, b0, e0);
+  ha(b0, tm[25], n[0], e1);
+  uint32_t f0, f1, f2, f3, q0, q1, q2, q3, h0, i0, i1;
+  fa(c[0], c[1], c[2], f0, q0);
+  fa(c[3], c[4], c[5], f1, q1);
+  fa(c[6], c[7], d0, f2, q2);
+  fa(d1, d2, e0, f3, q3);
+  fa(f0, f1, f2, h0, i0);
+  fa(f3, e1, h0, n[1], i1);
+  uint32_t j0, k0, j1, k1, k2;
+  fa(q0, q1, q2, j0, k0);
+  fa(q3, i0, i1, j1, k1);
+  ha(j0, j1, n[2], k2);
+  fa(k0, k1, k2, n[3], n[4]);
+}
+
+// Bit-sliced sum of two numbers of `bits` planes (LSB first), one more plane out.
+template <int BITS>
+__device__ __forceinline__ void add_planes(const uint32_t* a, const uint32_t* b, uint32_t* s) {
+  uint32_t carry = 0u;
+#pragma unroll
+  for (int i = 0; i < BITS; ++i) {
+    const uint32_t x = a[i] ^ b[i];
+    s[i] = x ^ carry;
+    carry = (a[i] & b[i]) | (carry & x);
+  }
+  s[BITS] = carry;
+}
+
+}  // namespace b4
+
+// Deposit modes of the 4D kernel.
+enum Bits4Mode : int { k4Smem = 0, k4Global = 1, k4Pairs = 2 };
+
+// Planes [w0, w1) of the block's column unit (tx, ty, tz). All threads of the
+// block call it; blockDim.x = 32 * k4Warps. sm: bits4_smem_words<NB>() words;
+// hist: the shared histogram (k4Smem).
+template <int NB, int CONV, int MODE>
+__device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t tz, int64_t w0,
+                           int64_t w1, bool fast, uint32_t* sm, int* hist) {
+  using namespace bits;
+  constexpr int EB = NB == 32 ? 4 : NB <= 8 ? 1 : 2;
+  constexpr int RAW = 8 * EB;
+  const unsigned FULL = 0xFFFFFFFFu, ALL = 0xFFFFFFFFu;
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const int64_t nw = im.n[0], nz = im.n[1], ny = im.n[2], nx = im.n[3];
+  const int64_t y = ty * kWcOwn - 1 + lane, x0 = tx * kWcOwn - 1;
+  const int64_t z = tz * k4ZB - 1 + wi;
+  bool vy[3], vz[3];
+#pragma unroll
+  for (int d = -1; d <= 1; ++d) {
+    vy[d + 1] = y + d >= 0 && y + d < ny;
+    vz[d + 1] = z + d >= 0 && z + d < nz;
+  }
+  uint32_t xin;
+  {
+    const int64_t lo = x0 < 0 ? -x0 : 0, hi = nx - x0 >= 32 ? 32 : nx - x0;
+    xin = (hi >= 32 ? FULL : ((1u << hi) - 1u)) & (FULL << lo);
+  }
+  const bool own = lane >= 1 && lane <= kWcOwn && wi >= 1 && wi <= k4ZB && vy[1] && vz[1];
+  const uint32_t dep = own ? (xin & 0x7FFFFFFEu) : 0u;
+  const uint32_t xo = ~xin;
+  const uint32_t cx[3] = {xo >> 1, xo, xo << 1};
+  const size_t row_bytes = (size_t)nx * EB;
+  const int ip = wi + 1 < k4Warps ? wi + 1 : wi, imn = wi > 0 ? wi - 1 : wi;
+
+  uint32_t* SP = sm;                                  // [2][k4Warps][NB][32]
+  uint32_t* GI = SP + 2 * k4Warps * NB * 32;          // [k4Warps][9][32]
+  uint32_t* GC = GI + k4Warps * 9 * 32;               // [2][k4Warps][27][32]
+  auto sp_at = [&](int64_t wv, int slice, int k) -> uint32_t* {
+    return SP + (((int)(wv & 1) * k4Warps + slice) * NB + k) * 32;
+  };
+  auto gc_at = [&](int64_t wv, int slice, int dz, int dy, int dx) -> uint32_t* {
+    return GC + (((int)(wv & 1) * k4Warps + slice) * 27 + (dz + 1) * 9 + (dy + 1) * 3 + dx + 1) * 32;
+  };
+  auto row_ptr = [&](int64_t wp) {
+    return im.img + (((size_t)(wp - im.w_mem_lo) * (size_t)nz + (size_t)z) * (size_t)ny +
+                     (size_t)y) * row_bytes;
+  };
+  auto load_raw = [&](int64_t wp, uint32_t* raw) {
+    if (!vy[1] || !vz[1] || wp < 0 || wp >= nw) return;
+    if (wp < im.w_mem_lo || wp >= im.w_mem_hi) {
+      atomicOr(im.err, kErrOverflow);
+      return;
+    }
+    if constexpr (EB == 4)
+      b4::load_window4(row_ptr(wp), x0, nx, fast, raw);
+    else
+      wc::load_window<EB>(row_ptr(wp), x0, nx, fast, raw);
+  };
+  // bit planes of a loaded row; value checks on the voxels inside the image
+  auto make_planes = [&](int64_t wp, uint32_t* raw, uint32_t* P) {
+    const uint32_t inside = (vy[1] && vz[1] && wp >= 0 && wp < nw) ? xin : 0u;
+    if constexpr (EB == 4) {
+      bool bad = false;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const float f = __uint_as_float(raw[i]);
+        bad = bad || (((inside >> i) & 1u) && value_bad(f));
+        raw[i] = value_key(f);
+      }
+      if (bad) atomicOr(im.err, kErrValue);
+      b4::transpose32(raw);
+#pragma unroll
+      for (int k = 0; k < 32; ++k) P[k] = raw[k];
+    } else if constexpr (EB == 1) {
+      transpose8(raw, P);
+    } else {
+      uint32_t lo[8], hi[8], ph[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        lo[j] = __byte_perm(raw[2 * j], raw[2 * j + 1], 0x6420);
+        hi[j] = __byte_perm(raw[2 * j], raw[2 * j + 1], 0x7531);
+      }
+      transpose8(lo, P);
+      transpose8(hi, ph);
+      uint32_t extra = 0;
+#pragma unroll
+      for (int k = 8; k < 16; ++k) {
+        if (k < NB) P[k] = ph[k - 8];
+        else extra |= ph[k - 8];
+      }
+      if (extra & inside) atomicOr(im.err, kErrValue);
+    }
+  };
+
+  uint32_t raw[RAW];
+#pragma unroll
+  for (int i = 0; i < RAW; ++i) raw[i] = 0u;
+  uint32_t P[NB], Q[NB];
+  const int64_t ws = w0 == 0 ? w0 : w0 - 1;
+  load_raw(ws, raw);
+  make_planes(ws, raw, P);
+  load_raw(ws + 1, raw);
+  make_planes(ws + 1, raw, Q);
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    sp_at(ws, wi, k)[lane] = P[k];
+    sp_at(ws + 1, wi, k)[lane] = Q[k];
+  }
+  if (w0 == 0) {
+    // no volume below the first: its exports are zero (every neighbour there
+    // is outside, i.e. after)
+#pragma unroll
+    for (int e = 0; e < 27; ++e) GC[(((int)((ws - 1) & 1) * k4Warps + wi) * 27 + e) * 32 + lane] = 0u;
+  }
+  __syncthreads();
+
+  for (int64_t w = ws; w < w1; ++w) {
+    if (w + 2 <= w1) load_raw(w + 2, raw);
+    // ---- the 40 forward comparisons, bit plane by bit plane
+    uint32_t bx = 0u, by[3], bz[3][3], bw[3][3][3];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+      const uint32_t c = P[k];
+      const uint32_t C[3] = {c >> 1, c, c << 1};  // [dx+1]: C[i + 1], C[i], C[i - 1]
+      const uint32_t ny1 = __shfl_down_sync(FULL, c, 1);
+      const uint32_t s1 = sp_at(w, ip, k)[lane];
+      const uint32_t zr[3] = {__shfl_up_sync(FULL, s1, 1), s1, __shfl_down_sync(FULL, s1, 1)};
+      const uint32_t qv[3] = {sp_at(w + 1, imn, k)[lane], Q[k], sp_at(w + 1, ip, k)[lane]};
+      uint32_t wr[3][3];
+#pragma unroll
+      for (int dz = 0; dz < 3; ++dz) {
+        wr[dz][0] = __shfl_up_sync(FULL, qv[dz], 1);
+        wr[dz][1] = qv[dz];
+        wr[dz][2] = __shfl_down_sync(FULL, qv[dz], 1);
+      }
+      auto chain = [&](uint32_t& b, uint32_t n, uint32_t cc) {
+        if (k == 0) {
+          b = cc & ~n;
+        } else {
+          const uint32_t nn = ~n;
+          b = (nn & cc) | (nn & b) | (cc & b);
+        }
+      };
+      chain(bx, c, C[2]);
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) {
+        chain(by[dx], ny1, C[dx]);
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+          chain(bz[dy][dx], zr[dy], C[dx]);
+#pragma unroll
+          for (int dz = 0; dz < 3; ++dz) chain(bw[dz][dy][dx], wr[dz][dy], C[dx]);
+        }
+      }
+    }
+    const bool w_in = w >= 0 && w < nw, w1_in = w + 1 >= 0 && w + 1 < nw;
+    const bool c_in = vy[1] && vz[1] && w_in;
+    const uint32_t co[3] = {c_in ? cx[0] : ALL, c_in ? cx[1] : ALL, c_in ? cx[2] : ALL};
+    const uint32_t Gx = gcmp(bx, co[2], c_in ? xo : ALL);
+    uint32_t Gy[3], Gz[3][3], Gw[3][3][3];
+#pragma unroll
+    for (int dx = 0; dx < 3; ++dx) {
+      Gy[dx] = gcmp(by[dx], co[dx], (vy[2] && vz[1] && w_in) ? xo : ALL);
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy) {
+        Gz[dy][dx] = gcmp(bz[dy][dx], co[dx], (vy[dy] && vz[2] && w_in) ? xo : ALL);
+#pragma unroll
+        for (int dz = 0; dz < 3; ++dz)
+          Gw[dz][dy][dx] = gcmp(bw[dz][dy][dx], co[dx], (vy[dy] && vz[dz] && w1_in) ? xo : ALL);
+      }
+    }
+    // ---- exports: to slice z + 1 (this step) and to volume w + 1 (next step)
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) {
+        GI[((wi * 9) + dy * 3 + dx) * 32 + lane] = Gz[dy][dx];
+#pragma unroll
+        for (int dz = 0; dz < 3; ++dz) gc_at(w, wi, dz - 1, dy - 1, dx - 1)[lane] = Gw[dz][dy][dx];
+      }
+    uint32_t Gydn[3];  // row y - 1's (0, 0, +1, dx) words
+#pragma unroll
+    for (int dx = 0; dx < 3; ++dx) Gydn[dx] = __shfl_up_sync(FULL, Gy[dx], 1);
+    __syncthreads();
+    // ---- the change evaluation and deposits
+    uint32_t nzm = 0u;
+    uint32_t A[5], Bp[5], Bm[5], bp = 0u, bm = 0u;
+    if (w >= w0 && dep) {
+      auto sh = [](uint32_t g, int dx) -> uint32_t { return dx > 0 ? g >> 1 : dx < 0 ? g << 1 : g; };
+      auto gen = [](uint32_t v) -> uint32_t { return CONV == kConvV ? v : ~v; };
+      uint32_t w0b[3][3][3], t[3][3][3];
+      // in-volume after-bits
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+          w0b[2][dy + 1][dx + 1] = gen(sh(Gz[dy + 1][dx + 1], dx));
+          w0b[0][dy + 1][dx + 1] =
+              gen(~GI[((imn * 9) + (1 - dy) * 3 + (1 - dx)) * 32 + ((lane + dy) & 31)]);
+        }
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        w0b[1][2][dx + 1] = gen(sh(Gy[dx + 1], dx));
+        w0b[1][0][dx + 1] = gen(~Gydn[1 - dx]);
+      }
+      w0b[1][1][2] = gen(sh(Gx, 1));
+      w0b[1][1][0] = gen(~Gx);
+      w0b[1][1][1] = 0u;
+      b4::count26(w0b, A);
+      // volume w + 1
+#pragma unroll
+      for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+          for (int dx = 0; dx < 3; ++dx) t[dz][dy][dx] = w0b[dz][dy][dx] & gen(sh(Gw[dz][dy][dx], dx - 1));
+      bp = gen(Gw[1][1][1]);
+      b4::count26(t, Bp);
+      // volume w - 1: the words volume w - 1 exported last step, complemented
+#pragma unroll
+      for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+          for (int dx = -1; dx <= 1; ++dx) {
+            const int sl = dz < 0 ? imn : dz > 0 ? ip : wi;
+            t[dz + 1][dy + 1][dx + 1] =
+                w0b[dz + 1][dy + 1][dx + 1] &
+                gen(~gc_at(w - 1, sl, -dz, -dy, -dx)[(lane + dy) & 31]);
+          }
+      bm = gen(~gc_at(w - 1, wi, 0, 0, 0)[lane]);
+      b4::count26(t, Bm);
+      // change = (13 + bp Bp + bm Bm) - (A + 13 bp + 13 bm); zero where both
+      // sides agree plane by plane
+      uint32_t L1[6], L[7], R1[6], R[7];
+      const uint32_t c13p[5] = {bp, 0u, bp, bp, 0u}, c13m[6] = {bm, 0u, bm, bm, 0u, 0u};
+      b4::add_planes<5>(A, c13p, L1);
+      b4::add_planes<6>(L1, c13m, L);
+      uint32_t xp[5], xm[5];
+#pragma unroll
+      for (int b = 0; b < 5; ++b) {
+        xp[b] = Bp[b] & bp;
+        xm[b] = Bm[b] & bm;
+      }
+      b4::add_planes<5>(xp, xm, R1);
+      const uint32_t c13[6] = {ALL, 0u, ALL, ALL, 0u, 0u};
+      b4::add_planes<6>(R1, c13, R);
+      uint32_t diff = 0u;
+#pragma unroll
+      for (int b = 0; b < 7; ++b) diff |= L[b] ^ R[b];
+      nzm = diff & dep;
+    }
+    // deposits: one voxel per lane and round (the pair append is warp-wide)
+    const unsigned char* rowz = row_ptr(w);
+    while (__any_sync(FULL, nzm != 0u)) {
+      const bool has = nzm != 0u;
+      int j = 0;
+      int change = 0;
+      uint32_t key = 0u;
+      if (has) {
+        j = __ffs(nzm) - 1;
+        nzm &= nzm - 1;
+        auto bitsof = [&](const uint32_t* v, int n) {
+          int r = 0;
+          for (int b = 0; b < n; ++b) r |= (int)((v[b] >> j) & 1u) << b;
+          return r;
+        };
+        const int a = bitsof(A, 5), p = bitsof(Bp, 5), m = bitsof(Bm, 5);
+        const int pb = (int)((bp >> j) & 1u), mb = (int)((bm >> j) & 1u);
+        change = (13 + pb * p + mb * m) - (a + 13 * pb + 13 * mb);
+        // the voxel's value (x0 + j >= 0: own bits are 1..30)
+        const unsigned char* vp = rowz + (size_t)(x0 + j) * EB;
+        if constexpr (EB == 4)
+          key = value_key(__ldg(reinterpret_cast<const float*>(vp)));
+        else if constexpr (EB == 2)
+          key = __ldg(reinterpret_cast<const unsigned short*>(vp));
+        else
+          key = __ldg(vp);
+      }
+      if constexpr (MODE == k4Pairs) {
+        emit_pair(has && change != 0, key, change, im.pairs, im.pair_count, im.pair_cap, im.err);
+      } else if (has && change != 0) {
+        const uint32_t v = key & ((1u << (NB < 32 ? NB : 31)) - 1u);
+        if (MODE == k4Smem)
+          atomicAdd(&hist[v], change);
+        else
+          atomicAdd(reinterpret_cast<unsigned long long*>(im.vcec) + v,
+                    (unsigned long long)(long long)change);
+      }
+    }
+    // ---- advance: the planes of w + 2 into the slot volume w frees
+    if (w + 2 <= w1) {
+#pragma unroll
+      for (int k = 0; k < NB; ++k) P[k] = Q[k];
+      make_planes(w + 2, raw, Q);
+#pragma unroll
+      for (int k = 0; k < NB; ++k) sp_at(w + 2, wi, k)[lane] = Q[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < NB; ++k) P[k] = Q[k];
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace ecc

@@ -99,13 +99,15 @@ bool is_device_ptr(const ecc_handle* h, const void* p) {
 }
 
 cudaError_t launch_local_bits(const LocalArgs& a, int num_sms, int64_t* launches);
+cudaError_t launch_local_bits4(const LocalArgs& a, int num_sms, int64_t* launches);
 
 // Kernel choice: the bit-sliced kernel where it applies (1-3D integer images
 // with 256, 16384 or 65536 bins and 16-byte aligned rows), the generic kernel
 // otherwise. variant 1 forces the generic kernel, 2 the bit-sliced one.
 cudaError_t launch_local(const LocalArgs& a, int num_sms, int64_t* launches) {
   if (a.variant != 1) {
-    cudaError_t e = launch_local_bits(a, num_sms, launches);
+    cudaError_t e = a.view == 4 ? launch_local_bits4(a, num_sms, launches)
+                                : launch_local_bits(a, num_sms, launches);
     if (e != cudaErrorNotSupported || a.variant == 2) return e;
     cudaGetLastError();
   }

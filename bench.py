@@ -382,6 +382,7 @@ def bench_batched(h, reqs, stream):
         k_ms.append(ecc.ecc_profile_span(h))
     same = all(np.array_equal(r.numpy(), b) for r, b in zip(ref, res))
     assert same, "batched curves differ from per-image curves"
+    bench_batched.curves = [np.array(b) for b in res]
     tp, tb, tc = min(t_per), min(t_bat), min(t_c)
     kernel_s = k_ms[int(np.argmin(t_c))] / 1e3
     return {"images": len(reqs), "voxels": int(vox), "per_image_s": tp, "batched_s": tb,
@@ -396,7 +397,15 @@ def bench_batched(h, reqs, stream):
                       "one's end (profiling events; the two slots' graphs overlap)"}
 
 
-def bench_serving(h, reqs, rate_hz: float, seed: int, borrowed: bool = False):
+def _same_curve(served, batched) -> bool:
+    """served (over at least as many bins) equals batched, then holds its last
+    value: thresholds past the largest image value add no cells."""
+    n = len(batched)
+    return (len(served) >= n and np.array_equal(served[:n], batched)
+            and bool(np.all(served[n:] == batched[-1])))
+
+
+def bench_serving(h, reqs, rate_hz: float, seed: int, borrowed: bool = False, ref=None):
     """Requests submitted at Poisson arrival times (rate_hz), polled to
     completion; latency = submit -> completion as recorded by the library.
     rate_hz = 0: all submitted at once (saturated). Request images are in
@@ -404,13 +413,21 @@ def bench_serving(h, reqs, rate_hz: float, seed: int, borrowed: bool = False):
     borrowed: ecc_submit_borrowed, which reads them in place instead of
     copying each before it returns. One untimed pass of the same requests on
     the same handle comes first (the warm-up of a long-running server: batch
-    graphs captured, result slabs and the device memory pool sized)."""
+    graphs captured, result slabs and the device memory pool sized). ref:
+    the curves of the same images from the batched call; every served curve
+    of the warm-up pass and every 16th of the timed pass must equal them (a
+    served curve spans the handle's default bins, 65536 for uint16, and past
+    the last batched bin it stays at the whole image's characteristic)."""
     from paper_1705_02045_gb300 import ecc
     submit = ecc.ecc_submit_borrowed if borrowed else ecc.ecc_submit
     warm = [submit(h, img) for img, _ in reqs]
-    for rid in warm:
-        st, _ = ecc.ecc_poll(h, rid, timeout_us=600_000_000)
+    checked = 0
+    for i, rid in enumerate(warm):
+        st, curve = ecc.ecc_poll(h, rid, timeout_us=600_000_000)
         assert st == ecc.ECC_OK
+        if ref is not None and i < len(ref):
+            assert _same_curve(curve, ref[i]), f"served curve {i} differs from the batched one"
+            checked += 1
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate_hz, size=len(reqs)) if rate_hz > 0 else np.zeros(len(reqs))
     arrivals = np.cumsum(gaps)
@@ -428,10 +445,19 @@ def bench_serving(h, reqs, rate_hz: float, seed: int, borrowed: bool = False):
     th = threading.Thread(target=submitter)
     th.start()
     th.join()
-    for rid in ids:
-        st, _ = ecc.ecc_poll(h, rid, timeout_us=600_000_000)
+    kept = {}
+    for i, rid in enumerate(ids):
+        st, curve = ecc.ecc_poll(h, rid, timeout_us=600_000_000)
         assert st == ecc.ECC_OK
+        if i % 16 == 0:
+            kept[i] = curve
     wall = time.perf_counter() - t0
+    if ref is not None:
+        for i, curve in kept.items():
+            if i < len(ref):
+                assert _same_curve(curve, ref[i]), f"served curve {i} differs from the batched one"
+                checked += 1
+    del kept
     lat = np.array([ecc.ecc_request_latency_us(h, rid) for rid in ids]) / 1e3
     # where the time went: submit -> copy seen done -> batch launched -> batch
     # seen done -> curve ready, for the median request and the slowest 1 %
@@ -440,9 +466,13 @@ def bench_serving(h, reqs, rate_hz: float, seed: int, borrowed: bool = False):
     slow = lat >= np.percentile(lat, 99)
     names = ["copy", "wait_launch", "batch", "complete"]
     vox = sum(int(np.prod(a.shape)) for a, _ in reqs)
+    sizes = np.array([int(np.prod(a.shape)) for a, _ in reqs], dtype=np.float64)
     return {"requests": len(reqs), "rate_hz": rate_hz, "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
             "gvox_s": vox / wall / 1e9, "wall_s": wall,
+            "curves_checked_against_batched": checked,
+            "mean_mvox_all": float(sizes.mean() / 1e6),
+            "mean_mvox_slowest_1pct": float(sizes[slow].mean() / 1e6),
             "stages_ms_median": {k: float(np.median(seg[:, i])) for i, k in enumerate(names)},
             "stages_ms_slowest_1pct": {k: float(seg[slow, i].mean()) for i, k in enumerate(names)}}
 
@@ -1023,17 +1053,19 @@ def main():
                 ecc.ecc_destroy(hb)
             if args.serve_requests > 0:
                 sreqs = [(torch.from_numpy(a).pin_memory(), b) for a, b in reqs[:args.serve_requests]]
+                # served curves are checked against the batched ones of the same images
+                ref = getattr(bench_batched, "curves", None)
                 def serve_pair(borrowed):
                     # saturated, then Poisson arrivals at 0.8x its throughput
                     hs = ecc.ecc_create(device=local)
                     try:
-                        sat = bench_serving(hs, sreqs, 0.0, synth.SEED_BASE + 4, borrowed)
+                        sat = bench_serving(hs, sreqs, 0.0, synth.SEED_BASE + 4, borrowed, ref)
                     finally:
                         ecc.ecc_destroy(hs)
                     rate = 0.8 * len(sreqs) / sat["wall_s"]
                     hs = ecc.ecc_create(device=local)
                     try:
-                        pois = bench_serving(hs, sreqs, rate, synth.SEED_BASE + 5, borrowed)
+                        pois = bench_serving(hs, sreqs, rate, synth.SEED_BASE + 5, borrowed, ref)
                     finally:
                         ecc.ecc_destroy(hs)
                     return {"poisson_0.8x": pois, "saturated": sat}

@@ -80,11 +80,13 @@ typedef struct ecc_config {
 /* Result of one image. Integer images: curve[t] = chi(K_t), t < bins.
  * Float images: the (threshold, chi) pairs at every value t where the VCEC
  * is non-zero, ascending in t; the curve is constant between them and 0 below
- * the first. Arrays are allocated by the library (owned = 1), or, for the
- * curves of ecc_compute_batch, lie in a pinned host block of the library
- * shared by a batch's results (owned = 2); either way they are released with
- * ecc_result_free (a shared block once all its results are released, also
- * after ecc_destroy). */
+ * the first. Arrays are allocated by the library (owned = 1), or lie in a
+ * pinned host block of the library (owned = 2): the curves of
+ * ecc_compute_batch and ecc_poll share one per batch, and the pairs of a float
+ * image from ecc_compute get one (chi first, thresholds after it) that the
+ * handle reuses for a later float image once this result is released. Either
+ * way they are released with ecc_result_free (a block once all its results
+ * are released, also after ecc_destroy). */
 typedef struct ecc_result {
   int64_t bins;
   int64_t* curve;

@@ -15,25 +15,37 @@
 // the same 3D offsets and b+- the straight w neighbours; each G_3 is 13 - N
 // with N the 26-term count of the 3D kernels.
 //
-// Layout: a block of 8 warps holds 8 consecutive z-slices of one 30 x 30
-// (y, x) tile (warps 0 and 7 are the z-collar, the 6 between own slices);
-// a warp holds 32 rows of its slice (lanes 0 and 31 the y-collar) and a lane
+// Layout: a block of 12 warps holds 12 consecutive z-slices of one 30 x 30
+// (y, x) tile, 10 own slices and the z-collar slice below and above them; a
+// warp holds 32 rows of its slice (lanes 0 and 31 the y-collar) and a lane
 // one 32-voxel word (bits 0 and 31 the x-collar), as in the warp-column
-// layout of the 3D kernel. The block marches along w; each lane keeps its
-// row's planes of volumes w and w + 1 in registers, the neighbouring slices'
-// planes come through shared memory (double-buffered by volume parity), rows
-// y +- 1 of a slice by warp shuffles. Comparison words travel to the later
-// voxel's row through shared memory: those with slice z + 1 within the step,
-// those with volume w + 1 to the next step. Two block barriers per step.
+// layout of the 3D kernel. The block marches along w; the bit planes of every
+// slice's rows in volumes w and w + 1 sit in shared memory (double-buffered
+// by volume parity), rows y +- 1 of a slice come by warp shuffles. The collar
+// warps advance only the borrow chains their own-slice neighbours read.
+// Comparison words travel to the later voxel's row through shared memory:
+// those with slice z + 1 within the step, those with volume w + 1 to the next
+// step. Two block barriers per step.
 #pragma once
+
+#include <type_traits>
 
 #include "ecc_bitsw.cuh"
 #include "ecc_device.cuh"
 
 namespace ecc {
 
-constexpr int k4ZB = 6;             // own z-slices per block
+constexpr int k4ZB = 10;            // own z-slices per block
 constexpr int k4Warps = k4ZB + 2;   // one warp per slice, the two collar slices included
+
+// Slice of warp wi (z = tz * k4ZB - 1 + slice): warps 0 .. k4ZB - 1 hold the
+// own slices 1 .. k4ZB, warp k4ZB the collar slice 0 below them and warp
+// k4ZB + 1 the collar slice above. The SM's four schedulers take warps by
+// index mod 4, so the two lighter collar warps go to two schedulers that
+// otherwise run two own warps each, the other two schedulers three own warps.
+__host__ __device__ constexpr int bits4_slice(int wi) {
+  return wi < k4ZB ? wi + 1 : (wi == k4ZB ? 0 : k4ZB + 1);
+}
 
 struct Bits4Img {
   const unsigned char* img;  // volume w_mem_lo
@@ -223,6 +235,13 @@ __device__ __forceinline__ void add_planes(const uint32_t* a, const uint32_t* b,
 // Deposit modes of the 4D kernel.
 enum Bits4Mode : int { k4Smem = 0, k4Global = 1, k4Pairs = 2 };
 
+// Borrow-chain groups of one bit plane (bits4_span): the comparisons with
+// slice z - 1 in volume w + 1 (A), with slice z + 1 in volumes w and w + 1 (B),
+// and those within the own slice (row x + 1, row y + 1, volume w + 1) (C). An
+// own slice advances all three, the collar slice below only B (its words with
+// slice z + 1 are the ones the first own slice reads), the one above only A.
+enum : int { k4GroupA = 1, k4GroupB = 2, k4GroupC = 4 };
+
 // Planes [w0, w1) of the block's column unit (tx, ty, tz). All threads of the
 // block call it; blockDim.x = 32 * k4Warps. sm: bits4_smem_words<NB>() words;
 // hist: the shared histogram (k4Smem).
@@ -234,9 +253,11 @@ __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t t
   constexpr int RAW = 8 * EB;
   const unsigned FULL = 0xFFFFFFFFu, ALL = 0xFFFFFFFFu;
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const int sl = bits4_slice(wi);
+  const int role = sl == 0 ? 1 : sl == k4ZB + 1 ? 2 : 0;  // own, collar below, collar above
   const int64_t nw = im.n[0], nz = im.n[1], ny = im.n[2], nx = im.n[3];
   const int64_t y = ty * kWcOwn - 1 + lane, x0 = tx * kWcOwn - 1;
-  const int64_t z = tz * k4ZB - 1 + wi;
+  const int64_t z = tz * k4ZB - 1 + sl;
   bool vy[3], vz[3];
 #pragma unroll
   for (int d = -1; d <= 1; ++d) {
@@ -248,14 +269,14 @@ __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t t
     const int64_t lo = x0 < 0 ? -x0 : 0, hi = nx - x0 >= 32 ? 32 : nx - x0;
     xin = (hi >= 32 ? FULL : ((1u << hi) - 1u)) & (FULL << lo);
   }
-  const bool own = lane >= 1 && lane <= kWcOwn && wi >= 1 && wi <= k4ZB && vy[1] && vz[1];
+  const bool own = role == 0 && lane >= 1 && lane <= kWcOwn && vy[1] && vz[1];
   const uint32_t dep = own ? (xin & 0x7FFFFFFEu) : 0u;
   const uint32_t xo = ~xin;
   const uint32_t cx[3] = {xo >> 1, xo, xo << 1};
   const size_t row_bytes = (size_t)nx * EB;
-  const int ip = wi + 1 < k4Warps ? wi + 1 : wi, imn = wi > 0 ? wi - 1 : wi;
+  const int ip = sl + 1 < k4Warps ? sl + 1 : sl, imn = sl > 0 ? sl - 1 : sl;
 
-  uint32_t* SP = sm;                                  // [2][k4Warps][NB][32]
+  uint32_t* SP = sm;                                  // [2][k4Warps][NB][32], by slice
   uint32_t* GI = SP + 2 * k4Warps * NB * 32;          // [k4Warps][9][32]
   uint32_t* GC = GI + k4Warps * 9 * 32;               // [2][k4Warps][27][32]
   auto sp_at = [&](int64_t wv, int slice, int k) -> uint32_t* {
@@ -279,7 +300,18 @@ __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t t
     else
       wc::load_window<EB>(row_ptr(wp), x0, nx, fast, raw);
   };
-  // bit planes of a loaded row; value checks on the voxels inside the image
+  // the row's bytes of volume wp into L2 (its first and last byte: at most
+  // 32 voxels + 2, two 128-byte lines for 4-byte values)
+  auto prefetch_row = [&](int64_t wp) {
+    if (!vy[1] || !vz[1] || wp < 0 || wp >= nw || wp < im.w_mem_lo || wp >= im.w_mem_hi) return;
+    const int64_t xa = x0 < 0 ? 0 : x0, xb = (x0 + 32 < nx ? x0 + 32 : nx) - 1;
+    const unsigned char* row = row_ptr(wp);
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(row + xa * EB));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(row + xb * EB));
+  };
+  // bit planes of a loaded row; value checks on the voxels inside the image.
+  // Rows outside the image keep whatever planes they get: every comparison
+  // with them is replaced through the outside masks.
   auto make_planes = [&](int64_t wp, uint32_t* raw, uint32_t* P) {
     const uint32_t inside = (vy[1] && vz[1] && wp >= 0 && wp < nw) ? xin : 0u;
     if constexpr (EB == 4) {
@@ -318,64 +350,102 @@ __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t t
   uint32_t raw[RAW];
 #pragma unroll
   for (int i = 0; i < RAW; ++i) raw[i] = 0u;
-  uint32_t P[NB], Q[NB];
+  uint32_t Y[NB];  // planes of the volume loaded ahead
   const int64_t ws = w0 == 0 ? w0 : w0 - 1;
   load_raw(ws, raw);
-  make_planes(ws, raw, P);
-  load_raw(ws + 1, raw);
-  make_planes(ws + 1, raw, Q);
+  make_planes(ws, raw, Y);
 #pragma unroll
-  for (int k = 0; k < NB; ++k) {
-    sp_at(ws, wi, k)[lane] = P[k];
-    sp_at(ws + 1, wi, k)[lane] = Q[k];
-  }
+  for (int k = 0; k < NB; ++k) sp_at(ws, sl, k)[lane] = Y[k];
+  load_raw(ws + 1, raw);
+  make_planes(ws + 1, raw, Y);
+#pragma unroll
+  for (int k = 0; k < NB; ++k) sp_at(ws + 1, sl, k)[lane] = Y[k];
   if (w0 == 0) {
     // no volume below the first: its exports are zero (every neighbour there
     // is outside, i.e. after)
 #pragma unroll
-    for (int e = 0; e < 27; ++e) GC[(((int)((ws - 1) & 1) * k4Warps + wi) * 27 + e) * 32 + lane] = 0u;
+    for (int e = 0; e < 27; ++e) GC[(((int)((ws - 1) & 1) * k4Warps + sl) * 27 + e) * 32 + lane] = 0u;
   }
+  // chains a slice's role does not advance keep these values
+  uint32_t bx = 0u, by[3] = {0u, 0u, 0u}, bz[3][3] = {}, bw[3][3][3] = {};
   __syncthreads();
 
   for (int64_t w = ws; w < w1; ++w) {
-    if (w + 2 <= w1) load_raw(w + 2, raw);
-    // ---- the 40 forward comparisons, bit plane by bit plane
-    uint32_t bx = 0u, by[3], bz[3][3], bw[3][3][3];
+    const bool more = w + 2 <= w1;
+    // volume w + 2 comes to L2 now and to registers after the comparisons
+    if (more) prefetch_row(w + 2);
+    // ---- the forward comparisons, bit plane by bit plane
+    // Each chain starts at 0 (no borrow) and takes the planes LSB first; the
+    // plane loop is unrolled only partly, the planes coming from shared memory.
+    constexpr int kUnroll = NB % 8 == 0 ? 8 : NB % 7 == 0 ? 7 : 1;
+    auto advance = [&](auto groups) {
+      constexpr int G = decltype(groups)::value;
 #pragma unroll
-    for (int k = 0; k < NB; ++k) {
-      const uint32_t c = P[k];
-      const uint32_t C[3] = {c >> 1, c, c << 1};  // [dx+1]: C[i + 1], C[i], C[i - 1]
-      const uint32_t ny1 = __shfl_down_sync(FULL, c, 1);
-      const uint32_t s1 = sp_at(w, ip, k)[lane];
-      const uint32_t zr[3] = {__shfl_up_sync(FULL, s1, 1), s1, __shfl_down_sync(FULL, s1, 1)};
-      const uint32_t qv[3] = {sp_at(w + 1, imn, k)[lane], Q[k], sp_at(w + 1, ip, k)[lane]};
-      uint32_t wr[3][3];
+      for (int i = 0; i < 3; ++i) {
+        if constexpr ((G & k4GroupC) != 0) by[i] = 0u;
 #pragma unroll
-      for (int dz = 0; dz < 3; ++dz) {
-        wr[dz][0] = __shfl_up_sync(FULL, qv[dz], 1);
-        wr[dz][1] = qv[dz];
-        wr[dz][2] = __shfl_down_sync(FULL, qv[dz], 1);
+        for (int j = 0; j < 3; ++j) {
+          if constexpr ((G & k4GroupA) != 0) bw[0][i][j] = 0u;
+          if constexpr ((G & k4GroupB) != 0) bz[i][j] = bw[2][i][j] = 0u;
+          if constexpr ((G & k4GroupC) != 0) bw[1][i][j] = 0u;
+        }
       }
-      auto chain = [&](uint32_t& b, uint32_t n, uint32_t cc) {
-        if (k == 0) {
-          b = cc & ~n;
-        } else {
+      if constexpr ((G & k4GroupC) != 0) bx = 0u;
+#pragma unroll kUnroll
+      for (int k = 0; k < NB; ++k) {
+        const uint32_t c = sp_at(w, sl, k)[lane];
+        const uint32_t C[3] = {c >> 1, c, c << 1};  // [dx+1]: C[i + 1], C[i], C[i - 1]
+        // borrow of n - cc through this plane: [n < cc] over the planes so far
+        auto chain = [&](uint32_t& b, uint32_t n, uint32_t cc) {
           const uint32_t nn = ~n;
           b = (nn & cc) | (nn & b) | (cc & b);
+        };
+        auto rows = [&](uint32_t q, uint32_t (&r)[3]) {
+          r[0] = __shfl_up_sync(FULL, q, 1);
+          r[1] = q;
+          r[2] = __shfl_down_sync(FULL, q, 1);
+        };
+        if constexpr ((G & k4GroupA) != 0) {
+          uint32_t r[3];
+          rows(sp_at(w + 1, imn, k)[lane], r);
+#pragma unroll
+          for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy) chain(bw[0][dy][dx], r[dy], C[dx]);
         }
-      };
-      chain(bx, c, C[2]);
+        if constexpr ((G & k4GroupB) != 0) {
+          uint32_t r[3], q[3];
+          rows(sp_at(w, ip, k)[lane], r);
+          rows(sp_at(w + 1, ip, k)[lane], q);
 #pragma unroll
-      for (int dx = 0; dx < 3; ++dx) {
-        chain(by[dx], ny1, C[dx]);
+          for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
-        for (int dy = 0; dy < 3; ++dy) {
-          chain(bz[dy][dx], zr[dy], C[dx]);
+            for (int dy = 0; dy < 3; ++dy) {
+              chain(bz[dy][dx], r[dy], C[dx]);
+              chain(bw[2][dy][dx], q[dy], C[dx]);
+            }
+        }
+        if constexpr ((G & k4GroupC) != 0) {
+          const uint32_t ny1 = __shfl_down_sync(FULL, c, 1);
+          uint32_t r[3];
+          rows(sp_at(w + 1, sl, k)[lane], r);
+          chain(bx, c, C[2]);
 #pragma unroll
-          for (int dz = 0; dz < 3; ++dz) chain(bw[dz][dy][dx], wr[dz][dy], C[dx]);
+          for (int dx = 0; dx < 3; ++dx) {
+            chain(by[dx], ny1, C[dx]);
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy) chain(bw[1][dy][dx], r[dy], C[dx]);
+          }
         }
       }
-    }
+    };
+    if (role == 0)
+      advance(std::integral_constant<int, k4GroupA | k4GroupB | k4GroupC>{});
+    else if (role == 1)
+      advance(std::integral_constant<int, k4GroupB>{});
+    else
+      advance(std::integral_constant<int, k4GroupA>{});
+    if (more) load_raw(w + 2, raw);
     const bool w_in = w >= 0 && w < nw, w1_in = w + 1 >= 0 && w + 1 < nw;
     const bool c_in = vy[1] && vz[1] && w_in;
     const uint32_t co[3] = {c_in ? cx[0] : ALL, c_in ? cx[1] : ALL, c_in ? cx[2] : ALL};
@@ -392,19 +462,33 @@ __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t t
           Gw[dz][dy][dx] = gcmp(bw[dz][dy][dx], co[dx], (vy[dy] && vz[dz] && w1_in) ? xo : ALL);
       }
     }
-    // ---- exports: to slice z + 1 (this step) and to volume w + 1 (next step)
+    // ---- exports: to slice z + 1 (this step) and to volume w + 1 (next step),
+    // the words some own slice reads
+    if (role != 2) {
 #pragma unroll
-    for (int dy = 0; dy < 3; ++dy)
+      for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-      for (int dx = 0; dx < 3; ++dx) {
-        GI[((wi * 9) + dy * 3 + dx) * 32 + lane] = Gz[dy][dx];
+        for (int dx = 0; dx < 3; ++dx) GI[((sl * 9) + dy * 3 + dx) * 32 + lane] = Gz[dy][dx];
+    }
 #pragma unroll
-        for (int dz = 0; dz < 3; ++dz) gc_at(w, wi, dz - 1, dy - 1, dx - 1)[lane] = Gw[dz][dy][dx];
+    for (int dz = 0; dz < 3; ++dz) {
+      if (role == 0 || (role == 1 && dz == 2) || (role == 2 && dz == 0)) {
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+          for (int dx = 0; dx < 3; ++dx) gc_at(w, sl, dz - 1, dy - 1, dx - 1)[lane] = Gw[dz][dy][dx];
       }
+    }
     uint32_t Gydn[3];  // row y - 1's (0, 0, +1, dx) words
 #pragma unroll
     for (int dx = 0; dx < 3; ++dx) Gydn[dx] = __shfl_up_sync(FULL, Gy[dx], 1);
+    // the planes of volume w + 2, stored once every warp is done with volume w
+    if (more) make_planes(w + 2, raw, Y);
     __syncthreads();
+    if (more) {
+#pragma unroll
+      for (int k = 0; k < NB; ++k) sp_at(w + 2, sl, k)[lane] = Y[k];
+    }
     // ---- the change evaluation and deposits
     uint32_t nzm = 0u;
     uint32_t A[5], Bp[5], Bm[5], bp = 0u, bm = 0u;
@@ -412,12 +496,13 @@ __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t t
       auto sh = [](uint32_t g, int dx) -> uint32_t { return dx > 0 ? g >> 1 : dx < 0 ? g << 1 : g; };
       auto gen = [](uint32_t v) -> uint32_t { return CONV == kConvV ? v : ~v; };
       uint32_t w0b[3][3][3], t[3][3][3];
-      // in-volume after-bits
+      // in-volume after-bits; the words this warp exported are read back from
+      // shared memory rather than kept in registers across the barrier
 #pragma unroll
       for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
         for (int dx = -1; dx <= 1; ++dx) {
-          w0b[2][dy + 1][dx + 1] = gen(sh(Gz[dy + 1][dx + 1], dx));
+          w0b[2][dy + 1][dx + 1] = gen(sh(GI[((sl * 9) + (dy + 1) * 3 + (dx + 1)) * 32 + lane], dx));
           w0b[0][dy + 1][dx + 1] =
               gen(~GI[((imn * 9) + (1 - dy) * 3 + (1 - dx)) * 32 + ((lane + dy) & 31)]);
         }
@@ -436,8 +521,9 @@ __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t t
 #pragma unroll
         for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-          for (int dx = 0; dx < 3; ++dx) t[dz][dy][dx] = w0b[dz][dy][dx] & gen(sh(Gw[dz][dy][dx], dx - 1));
-      bp = gen(Gw[1][1][1]);
+          for (int dx = 0; dx < 3; ++dx)
+            t[dz][dy][dx] = w0b[dz][dy][dx] & gen(sh(gc_at(w, sl, dz - 1, dy - 1, dx - 1)[lane], dx - 1));
+      bp = gen(gc_at(w, sl, 0, 0, 0)[lane]);
       b4::count26(t, Bp);
       // volume w - 1: the words volume w - 1 exported last step, complemented
 #pragma unroll
@@ -446,12 +532,12 @@ __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t t
         for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
           for (int dx = -1; dx <= 1; ++dx) {
-            const int sl = dz < 0 ? imn : dz > 0 ? ip : wi;
+            const int sn = dz < 0 ? imn : dz > 0 ? ip : sl;
             t[dz + 1][dy + 1][dx + 1] =
                 w0b[dz + 1][dy + 1][dx + 1] &
-                gen(~gc_at(w - 1, sl, -dz, -dy, -dx)[(lane + dy) & 31]);
+                gen(~gc_at(w - 1, sn, -dz, -dy, -dx)[(lane + dy) & 31]);
           }
-      bm = gen(~gc_at(w - 1, wi, 0, 0, 0)[lane]);
+      bm = gen(~gc_at(w - 1, sl, 0, 0, 0)[lane]);
       b4::count26(t, Bm);
       // change = (13 + bp Bp + bm Bm) - (A + 13 bp + 13 bm); zero where both
       // sides agree plane by plane
@@ -510,17 +596,6 @@ __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t t
           atomicAdd(reinterpret_cast<unsigned long long*>(im.vcec) + v,
                     (unsigned long long)(long long)change);
       }
-    }
-    // ---- advance: the planes of w + 2 into the slot volume w frees
-    if (w + 2 <= w1) {
-#pragma unroll
-      for (int k = 0; k < NB; ++k) P[k] = Q[k];
-      make_planes(w + 2, raw, Q);
-#pragma unroll
-      for (int k = 0; k < NB; ++k) sp_at(w + 2, wi, k)[lane] = Q[k];
-    } else {
-#pragma unroll
-      for (int k = 0; k < NB; ++k) P[k] = Q[k];
     }
     __syncthreads();
   }

@@ -72,11 +72,12 @@ cudaError_t launch_scan(const long long* vcec, long long* curve, int64_t bins,
                         cudaStream_t stream, int64_t* launches);
 
 // Float path: sorts `n` packed pairs by key (radix sort on the high 32 bits),
-// reduces equal keys, drops zero sums and prefix-sums: writes out_keys[k],
-// out_chi[k] and *out_count. Temporary buffers come from `tmp` (bytes).
+// reduces equal keys, drops zero sums and prefix-sums: writes out_vals[k]
+// (the thresholds as float32 bit patterns), out_chi[k] and *out_count.
+// Temporary buffers come from `tmp` (bytes).
 size_t float_tail_tmp_bytes(int64_t n);
 cudaError_t launch_float_tail(unsigned long long* pairs, int64_t n, void* tmp,
-                              size_t tmp_bytes, uint32_t* out_keys, long long* out_chi,
+                              size_t tmp_bytes, uint32_t* out_vals, long long* out_chi,
                               unsigned long long* out_count, cudaStream_t stream,
                               int64_t* launches);
 

@@ -386,11 +386,36 @@ static int err_word_status(ecc_handle* h, int word) {
   return ECC_OK;
 }
 
-static float key_to_float(uint32_t k) {
-  const uint32_t b = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
-  float f;
-  std::memcpy(&f, &b, 4);
-  return f;
+// A pinned block of at least `need` bytes for one float image's pairs, with
+// one reference for the result (and one the handle keeps): a block of the
+// handle's that no result references any more, else a new one. The handle
+// keeps at most kPairBlocks; a block it lets go lives on until its result is
+// released.
+constexpr size_t kPairBlocks = 3;
+static ResultBlock* take_pair_block(ecc_handle* h, size_t need) {
+  for (ResultBlock* b : h->pair_blocks) {
+    // refs == 1: only the handle's reference; no other thread can add one
+    if (b->cap >= need && b->refs.load(std::memory_order_acquire) == 1) {
+      b->refs.fetch_add(1, std::memory_order_acq_rel);
+      return b;
+    }
+  }
+  const size_t cap = std::max<size_t>(need + need / 4, size_t(1) << 20);
+  void* p = nullptr;
+  if (cudaHostAlloc(&p, cap, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  ResultBlock* b = new ResultBlock();
+  b->p = static_cast<unsigned char*>(p);
+  b->cap = cap;
+  b->refs.store(2);
+  if (h->pair_blocks.size() >= kPairBlocks) {
+    result_block_release(h->pair_blocks.front());
+    h->pair_blocks.erase(h->pair_blocks.begin());
+  }
+  h->pair_blocks.push_back(b);
+  return b;
 }
 
 // Float pairs of an image on the device. With n_chunks > 0 the image is still
@@ -404,7 +429,7 @@ static int compute_float(ecc_handle* h, const void* d_img, const Shape& s, ecc_r
   if ((e = h->pairs.ensure(sizeof(unsigned long long) * std::max<int64_t>(n, 1))) ||
       (e = h->pair_count.ensure(sizeof(unsigned long long))) ||
       (e = h->tmp.ensure(float_tail_tmp_bytes(n))) ||
-      (e = h->out_keys.ensure(sizeof(uint32_t) * std::max<int64_t>(n, 1))) ||
+      (e = h->out_vals.ensure(sizeof(uint32_t) * std::max<int64_t>(n, 1))) ||
       (e = h->out_chi.ensure(sizeof(long long) * std::max<int64_t>(n, 1))) ||
       (e = h->out_count.ensure(sizeof(unsigned long long))))
     return cuda_err(h, e, "float buffers");
@@ -456,7 +481,7 @@ static int compute_float(ecc_handle* h, const void* d_img, const Shape& s, ecc_r
   if ((rc = err_word_status(h, word))) return rc;
   cnt = 0;
   if ((e = launch_float_tail(h->pairs.as<unsigned long long>(), (int64_t)npairs, h->tmp.p,
-                             h->tmp.cap, h->out_keys.as<uint32_t>(), h->out_chi.as<long long>(),
+                             h->tmp.cap, h->out_vals.as<uint32_t>(), h->out_chi.as<long long>(),
                              h->out_count.as<unsigned long long>(), st, &cnt)))
     return cuda_err(h, e, "float tail");
   h->launches += cnt;
@@ -464,18 +489,27 @@ static int compute_float(ecc_handle* h, const void* d_img, const Shape& s, ecc_r
   if ((e = cudaMemcpyAsync(&k, h->out_count.p, 8, cudaMemcpyDeviceToHost, st)))
     return cuda_err(h, e, "copy count");
   if ((rc = sync_stream(h, st))) return rc;
-  std::vector<uint32_t> keys(k);
   out->npairs = (int64_t)k;
-  out->thresholds = static_cast<float*>(std::malloc(sizeof(float) * std::max<uint64_t>(k, 1)));
-  out->chi = static_cast<int64_t*>(std::malloc(sizeof(int64_t) * std::max<uint64_t>(k, 1)));
-  if (!out->thresholds || !out->chi) return set_err(h, ECC_ERR_OOM, "host result");
-  if (k) {
-    if ((e = cudaMemcpyAsync(keys.data(), h->out_keys.p, 4 * k, cudaMemcpyDeviceToHost, st)) ||
-        (e = cudaMemcpyAsync(out->chi, h->out_chi.p, 8 * k, cudaMemcpyDeviceToHost, st)))
-      return cuda_err(h, e, "copy pairs");
-    if ((rc = sync_stream(h, st))) return rc;
+  if (k == 0) {
+    out->thresholds = static_cast<float*>(std::malloc(sizeof(float)));
+    out->chi = static_cast<int64_t*>(std::malloc(sizeof(int64_t)));
+    if (!out->thresholds || !out->chi) return set_err(h, ECC_ERR_OOM, "host result");
+    return ECC_OK;
   }
-  for (uint64_t i = 0; i < k; ++i) out->thresholds[i] = key_to_float(keys[i]);
+  // [header][chi: 8k bytes][thresholds: 4k bytes] in a pinned block
+  const size_t need = kResultHeader + 12 * (size_t)k;
+  ResultBlock* blk = take_pair_block(h, need);
+  if (!blk) return set_err(h, ECC_ERR_OOM, "pinned result block of %zu bytes", need);
+  uint64_t* hdr = reinterpret_cast<uint64_t*>(blk->p);
+  hdr[0] = reinterpret_cast<uint64_t>(blk);
+  hdr[1] = kResultMagic;
+  out->chi = reinterpret_cast<int64_t*>(blk->p + kResultHeader);
+  out->thresholds = reinterpret_cast<float*>(blk->p + kResultHeader + 8 * (size_t)k);
+  out->owned = 2;  // the result's reference to blk; released by ecc_result_free
+  if ((e = cudaMemcpyAsync(out->chi, h->out_chi.p, 8 * k, cudaMemcpyDeviceToHost, st)) ||
+      (e = cudaMemcpyAsync(out->thresholds, h->out_vals.p, 4 * k, cudaMemcpyDeviceToHost, st)))
+    return cuda_err(h, e, "copy pairs");
+  if ((rc = sync_stream(h, st))) return rc;
   return ECC_OK;
 }
 
@@ -577,7 +611,7 @@ void ecc_destroy(ecc_handle* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
   for (DevBuf* b : {&h->img, &h->vcec, &h->curve, &h->errw, &h->pairs, &h->pair_count, &h->tmp,
-                    &h->out_keys, &h->out_chi, &h->out_count, &h->batch_desc, &h->batch_items,
+                    &h->out_vals, &h->out_chi, &h->out_count, &h->batch_desc, &h->batch_items,
                     &h->batch_vcec, &h->batch_curve, &h->codes, &h->done})
     b->release();
   for (auto& pr : h->prof_events) {
@@ -585,6 +619,7 @@ void ecc_destroy(ecc_handle* h) {
     cudaEventDestroy(pr.second);
   }
   for (cudaEvent_t ev : h->prof_pool) cudaEventDestroy(ev);
+  for (ResultBlock* b : h->pair_blocks) result_block_release(b);
   delete h->tuner;
   if (h->h_err) cudaFreeHost(h->h_err);
   if (h->h_curve) cudaFreeHost(h->h_curve);
@@ -603,13 +638,13 @@ const char* ecc_last_error(const ecc_handle* h) {
 void ecc_result_free(ecc_result* r) {
   if (!r) return;
   if (r->owned == 2) {
-    // a curve inside a batch's pinned result block: drop its reference
-    if (r->curve) {
-      const uint64_t* hdr = reinterpret_cast<const uint64_t*>(r->curve) - 2;
+    // a curve (or the chi array of float pairs, the thresholds after it)
+    // inside a pinned result block: drop its reference
+    const void* first = r->curve ? static_cast<const void*>(r->curve) : r->chi;
+    if (first) {
+      const uint64_t* hdr = reinterpret_cast<const uint64_t*>(first) - 2;
       if (hdr[1] == kResultMagic) result_block_release(reinterpret_cast<ResultBlock*>(hdr[0]));
     }
-    std::free(r->thresholds);
-    std::free(r->chi);
   } else if (r->owned) {
     std::free(r->curve);
     std::free(r->thresholds);

@@ -104,7 +104,7 @@ struct ecc_handle {
   std::atomic<int64_t> launches{0};
   int64_t launch_tmp = 0;
 
-  ecc::DevBuf img, vcec, curve, errw, pairs, pair_count, tmp, out_keys, out_chi, out_count;
+  ecc::DevBuf img, vcec, curve, errw, pairs, pair_count, tmp, out_vals, out_chi, out_count;
   ecc::DevBuf codes;                    // value-transform codes (ecc_compute_quantized)
   ecc::DevBuf done;                     // block counter of the fused curve scan (kept at 0)
   const void* clean_vcec = nullptr;     // vcec buffer known to be zero on its first
@@ -116,6 +116,10 @@ struct ecc_handle {
   cudaEvent_t sync_ev = nullptr;        // bounded waits of the blocking calls
   int64_t* h_curve = nullptr;           // pinned staging of integer curves
   size_t h_curve_cap = 0;               // entries of h_curve
+  // pinned blocks the (threshold, chi) pairs of float images are copied into
+  // (results owned = 2); the handle holds one reference to each, and a block
+  // only it still references is reused by the next float image
+  std::vector<ecc::ResultBlock*> pair_blocks;
 
   // instrumentation: event pairs around contribution kernels
   bool prof_on = false;

@@ -261,7 +261,7 @@ k_nz_totals(const long long* __restrict__ e_p, const unsigned* __restrict__ m_pt
 __global__ void __launch_bounds__(kSThreads)
 k_nz_emit(const uint32_t* __restrict__ e_key, const long long* __restrict__ e_p,
           const unsigned* __restrict__ m_ptr, const unsigned* __restrict__ tile_nz,
-          uint32_t* __restrict__ out_key, long long* __restrict__ out_chi) {
+          uint32_t* __restrict__ out_val, long long* __restrict__ out_chi) {
   const int64_t m = *m_ptr;
   const int64_t base = (int64_t)blockIdx.x * kSTile + (int64_t)threadIdx.x * kSItems;
   unsigned cnt = 0;
@@ -274,7 +274,10 @@ k_nz_emit(const uint32_t* __restrict__ e_key, const long long* __restrict__ e_p,
   for (int j = 0; j < kSItems; ++j) {
     const int64_t k = base + j;
     if (k < m && nz_at(e_p, k)) {
-      out_key[pos] = e_key[k];
+      // the threshold itself: the order-preserving key mapped back to the
+      // float's bits (negative values were stored complemented)
+      const uint32_t key = e_key[k];
+      out_val[pos] = (key & 0x80000000u) ? (key & 0x7FFFFFFFu) : ~key;
       out_chi[pos] = e_p[k];
       ++pos;
     }
@@ -312,7 +315,7 @@ TmpLayout layout(int64_t n) {
 size_t float_tail_tmp_bytes(int64_t n) { return layout(n).total; }
 
 cudaError_t launch_float_tail(unsigned long long* pairs, int64_t n, void* tmp, size_t tmp_bytes,
-                              uint32_t* out_keys, long long* out_chi,
+                              uint32_t* out_vals, long long* out_chi,
                               unsigned long long* out_count, cudaStream_t stream,
                               int64_t* launches) {
   const TmpLayout L = layout(n);
@@ -352,7 +355,7 @@ cudaError_t launch_float_tail(unsigned long long* pairs, int64_t n, void* tmp, s
   k_seg_emit<<<(unsigned)sb, kSThreads, 0, stream>>>(a, n, tile_sum, tile_ends, e_key, e_p);
   k_nz_totals<<<(unsigned)sb, kSThreads, 0, stream>>>(e_p, m, tile_nz);
   k_scan_tiles<unsigned><<<1, kSThreads, 0, stream>>>(tile_nz, sb, nz);
-  k_nz_emit<<<(unsigned)sb, kSThreads, 0, stream>>>(e_key, e_p, m, tile_nz, out_keys, out_chi);
+  k_nz_emit<<<(unsigned)sb, kSThreads, 0, stream>>>(e_key, e_p, m, tile_nz, out_vals, out_chi);
   k_count_to_u64<<<1, 1, 0, stream>>>(nz, out_count);
   *launches += 8;
   return cudaGetLastError();

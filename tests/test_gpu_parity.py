@@ -128,6 +128,38 @@ def test_4d_several_x_tiles(hV, hT, conv, shape, kind):
 
 
 @pytest.mark.parametrize("conv", ["V", "T"])
+@pytest.mark.parametrize("shape,kind", [
+    ((4, 23, 9, 40), "u8"), ((3, 20, 6, 31), "u8"), ((2, 1, 5, 33), "u8"),
+    ((3, 31, 5, 70), "u16_14"), ((2, 11, 33, 9), "u16"),
+    ((3, 21, 31, 33), "f32"), ((4, 10, 7, 20), "f32"), ((2, 12, 3, 62), "f32")], ids=str)
+def test_4d_several_z_tiles(hV, hT, conv, shape, kind):
+    """4D images whose z extent crosses the 4D kernel's blocks of own
+    z-slices (exact multiples, ragged tails, a single slice), in every value
+    mode: shared histogram (u8, 14-bit u16), global histogram (65536 bins)
+    and pairs (f32)."""
+    h = _handle(hV, hT, conv)
+    if kind == "u8":
+        img = synth.smooth_u8(shape, 1.5, S + 58)
+        assert np.array_equal(ecc.ecc_compute(h, img), oracle.ecc_int(img, 256, conv))
+    elif kind == "u16_14":
+        img = synth.two_phase_u16(shape, 1.5, S + 59)
+        h14 = ecc.ecc_create(device=0, bins=16384, convention=0 if conv == "V" else 1)
+        try:
+            got = ecc.ecc_compute(h14, img)
+        finally:
+            ecc.ecc_destroy(h14)
+        assert np.array_equal(got, oracle.ecc_int(img, 16384, conv))
+    elif kind == "u16":
+        img = synth.uniform_int(shape, 65536, S + 60, np.uint16)
+        assert np.array_equal(ecc.ecc_compute(h, img), oracle.ecc_int(img, 65536, conv))
+    else:
+        img = synth.grf_f32(shape, 1.5, S + 61)
+        t, chi = ecc.ecc_compute(h, img)
+        t_ref, chi_ref = oracle.ecc_pairs_float(img, conv)
+        assert np.array_equal(t, t_ref) and np.array_equal(chi, chi_ref)
+
+
+@pytest.mark.parametrize("conv", ["V", "T"])
 def test_f32_4d_full_size_equals_oracle(tmp_path, conv):
     """The 128^4 float field of the benchmark (Gaussian random field, sigma = 3
     per axis), element by element against the oracle over the whole image:

@@ -81,21 +81,34 @@ constexpr size_t bits4_smem_words() {
 
 namespace b4 {
 
-// 32 x 32 bit transpose by five delta swaps: afterwards A[k] bit j = bit k of
-// the original A[j].
+// 32 x 32 bit transpose: afterwards A[k] bit j = bit k of the original A[j].
+// The 16- and 8-bit stages exchange half-words and bytes with one byte
+// permutation per output word; the 4-, 2- and 1-bit stages are delta swaps.
 __device__ __forceinline__ void transpose32(uint32_t A[32]) {
-  const uint32_t M[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
 #pragma unroll
-  for (int st = 0; st < 5; ++st) {
-    const int s = 16 >> st;
+  for (int j = 0; j < 16; ++j) {
+    const uint32_t a = A[j], b = A[j | 16];
+    A[j] = __byte_perm(a, b, 0x5410);       // low halves of a and b
+    A[j | 16] = __byte_perm(a, b, 0x7632);  // high halves
+  }
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    if (j & 8) continue;
+    const uint32_t a = A[j], b = A[j | 8];
+    A[j] = __byte_perm(a, b, 0x6240);      // bytes 0, 2 of a and b
+    A[j | 8] = __byte_perm(a, b, 0x7351);  // bytes 1, 3
+  }
+  const uint32_t M[3] = {0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int st = 0; st < 3; ++st) {
+    const int s = 4 >> st;
     const uint32_t m = M[st];
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       if (j & s) continue;
       const uint32_t a = A[j], b = A[j | s];
-      const uint32_t t = ((a >> s) ^ b) & m;
-      A[j] = a ^ (t << s);
-      A[j | s] = b ^ t;
+      A[j] = (a & m) | ((b << s) & ~m);
+      A[j | s] = ((a >> s) & m) | (b & ~m);
     }
   }
 }
@@ -491,8 +504,9 @@ __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t t
     }
     // ---- the change evaluation and deposits
     uint32_t nzm = 0u;
-    uint32_t A[5], Bp[5], Bm[5], bp = 0u, bm = 0u;
+    uint32_t D[8];  // the change as 8-bit two's complement planes
     if (w >= w0 && dep) {
+      uint32_t A[5], Bp[5], Bm[5], bp = 0u, bm = 0u;
       auto sh = [](uint32_t g, int dx) -> uint32_t { return dx > 0 ? g >> 1 : dx < 0 ? g << 1 : g; };
       auto gen = [](uint32_t v) -> uint32_t { return CONV == kConvV ? v : ~v; };
       uint32_t w0b[3][3][3], t[3][3][3];
@@ -554,10 +568,17 @@ __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t t
       b4::add_planes<5>(xp, xm, R1);
       const uint32_t c13[6] = {ALL, 0u, ALL, ALL, 0u, 0u};
       b4::add_planes<6>(R1, c13, R);
-      uint32_t diff = 0u;
+      // D = R - L = R + ~L + 1 over 8 planes (L, R < 128)
+      uint32_t carry = ALL, any = 0u;
 #pragma unroll
-      for (int b = 0; b < 7; ++b) diff |= L[b] ^ R[b];
-      nzm = diff & dep;
+      for (int b = 0; b < 8; ++b) {
+        const uint32_t lb = b < 7 ? ~L[b] : ALL, rb = b < 7 ? R[b] : 0u;
+        const uint32_t x = rb ^ lb;
+        D[b] = x ^ carry;
+        carry = (rb & lb) | (carry & x);
+        any |= D[b];
+      }
+      nzm = any & dep;
     }
     // deposits: one voxel per lane and round (the pair append is warp-wide)
     const unsigned char* rowz = row_ptr(w);
@@ -569,14 +590,10 @@ __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t t
       if (has) {
         j = __ffs(nzm) - 1;
         nzm &= nzm - 1;
-        auto bitsof = [&](const uint32_t* v, int n) {
-          int r = 0;
-          for (int b = 0; b < n; ++b) r |= (int)((v[b] >> j) & 1u) << b;
-          return r;
-        };
-        const int a = bitsof(A, 5), p = bitsof(Bp, 5), m = bitsof(Bm, 5);
-        const int pb = (int)((bp >> j) & 1u), mb = (int)((bm >> j) & 1u);
-        change = (13 + pb * p + mb * m) - (a + 13 * pb + 13 * mb);
+        int v = 0;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) v |= (int)((D[b] >> j) & 1u) << b;
+        change = (int)(signed char)v;
         // the voxel's value (x0 + j >= 0: own bits are 1..30)
         const unsigned char* vp = rowz + (size_t)(x0 + j) * EB;
         if constexpr (EB == 4)

@@ -72,6 +72,10 @@ inline Bits4Geo bits4_geo(int64_t nz, int64_t ny, int64_t nx) {
   return g;
 }
 
+// Pairs a warp gathers in shared memory before appending them to the global
+// list (one atomic on its counter per flush).
+constexpr int k4PairBuf = 64;
+
 // Shared-memory words of one block: planes of both volumes for every slice,
 // the in-volume exports to slice z + 1, the cross exports of two steps.
 template <int NB>
@@ -257,7 +261,8 @@ enum : int { k4GroupA = 1, k4GroupB = 2, k4GroupC = 4 };
 
 // Planes [w0, w1) of the block's column unit (tx, ty, tz). All threads of the
 // block call it; blockDim.x = 32 * k4Warps. sm: bits4_smem_words<NB>() words;
-// hist: the shared histogram (k4Smem).
+// hist: the shared histogram (k4Smem) or the warps' pair buffers (k4Pairs,
+// k4Warps x k4PairBuf 8-byte entries; flushed before return).
 template <int NB, int CONV, int MODE>
 __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t tz, int64_t w0,
                            int64_t w1, bool fast, uint32_t* sm, int* hist) {
@@ -288,6 +293,24 @@ __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t t
   const uint32_t cx[3] = {xo >> 1, xo, xo << 1};
   const size_t row_bytes = (size_t)nx * EB;
   const int ip = sl + 1 < k4Warps ? sl + 1 : sl, imn = sl > 0 ? sl - 1 : sl;
+  // k4Pairs: this warp's pair buffer and its fill (the same in every lane)
+  unsigned long long* pbuf = reinterpret_cast<unsigned long long*>(hist) + wi * k4PairBuf;
+  int pfill = 0;
+  auto flush_pairs = [&]() {
+    if (pfill == 0) return;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(im.pair_count, (unsigned long long)pfill);
+    base = __shfl_sync(FULL, base, 0);
+    for (int i = lane; i < pfill; i += 32) {
+      const unsigned long long slot = base + (unsigned long long)i;
+      if ((int64_t)slot < im.pair_cap)
+        im.pairs[slot] = pbuf[i];
+      else
+        atomicOr(im.err, kErrOverflow);
+    }
+    __syncwarp();
+    pfill = 0;
+  };
 
   uint32_t* SP = sm;                                  // [2][k4Warps][NB][32], by slice
   uint32_t* GI = SP + 2 * k4Warps * NB * 32;          // [k4Warps][9][32]
@@ -328,15 +351,24 @@ __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t t
   auto make_planes = [&](int64_t wp, uint32_t* raw, uint32_t* P) {
     const uint32_t inside = (vy[1] && vz[1] && wp >= 0 && wp < nw) ? xin : 0u;
     if constexpr (EB == 4) {
-      bool bad = false;
+      // order-preserving keys: -0.0 as +0.0, negative values complemented,
+      // the sign bit set on the others
 #pragma unroll
       for (int i = 0; i < 32; ++i) {
-        const float f = __uint_as_float(raw[i]);
-        bad = bad || (((inside >> i) & 1u) && value_bad(f));
-        raw[i] = value_key(f);
+        const uint32_t b = raw[i] == 0x80000000u ? 0u : raw[i];
+        raw[i] = b ^ ((uint32_t)((int32_t)b >> 31) | 0x80000000u);
       }
-      if (bad) atomicOr(im.err, kErrValue);
       b4::transpose32(raw);
+      // Inf / NaN (exponent all ones), tested on the key planes: a value of
+      // either sign keeps its exponent bits in key bits 23..30, complemented
+      // when negative (key bit 31 clear)
+      uint32_t e1 = raw[23], e0 = raw[23];
+#pragma unroll
+      for (int k = 24; k <= 30; ++k) {
+        e1 &= raw[k];
+        e0 |= raw[k];
+      }
+      if (((e1 & raw[31]) | (~e0 & ~raw[31])) & inside) atomicOr(im.err, kErrValue);
 #pragma unroll
       for (int k = 0; k < 32; ++k) P[k] = raw[k];
     } else if constexpr (EB == 1) {
@@ -604,7 +636,15 @@ __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t t
           key = __ldg(vp);
       }
       if constexpr (MODE == k4Pairs) {
-        emit_pair(has && change != 0, key, change, im.pairs, im.pair_count, im.pair_cap, im.err);
+        // into the warp's buffer (every lane with a voxel has a non-zero change)
+        const unsigned ballot = __ballot_sync(FULL, has);
+        const int n = __popc(ballot);
+        if (pfill + n > k4PairBuf) flush_pairs();
+        if (has)
+          pbuf[pfill + __popc(ballot & ((1u << lane) - 1u))] =
+              ((unsigned long long)key << 32) | (uint32_t)change;
+        __syncwarp();
+        pfill += n;
       } else if (has && change != 0) {
         const uint32_t v = key & ((1u << (NB < 32 ? NB : 31)) - 1u);
         if (MODE == k4Smem)
@@ -616,6 +656,7 @@ __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t t
     }
     __syncthreads();
   }
+  if constexpr (MODE == k4Pairs) flush_pairs();
 }
 
 }  // namespace ecc

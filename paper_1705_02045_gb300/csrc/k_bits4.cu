@@ -74,7 +74,9 @@ cudaError_t launch4(const LocalArgs& a, int num_sms, int64_t* launches) {
   im.pairs = a.pairs;
   im.pair_count = a.pair_count;
   im.pair_cap = a.pair_cap;
-  const size_t smem = bits4_smem_words<NB>() * 4 + (MODE == k4Smem ? sizeof(int) * (size_t)a.bins : 0);
+  const size_t smem = bits4_smem_words<NB>() * 4 +
+                      (MODE == k4Smem ? sizeof(int) * (size_t)a.bins
+                       : MODE == k4Pairs ? sizeof(unsigned long long) * k4Warps * k4PairBuf : 0);
   auto kern = k_bits4<NB, CONV, MODE>;
   int per_sm = 0;
   cudaError_t e = blocks_per_sm(kern, 32 * k4Warps, smem, &per_sm);

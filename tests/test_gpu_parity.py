@@ -314,6 +314,37 @@ def test_nan_inf_rejected(hV, bad):
     assert ei.value.status == ecc.ECC_ERR_VALUE
 
 
+@pytest.mark.parametrize("bad", [np.nan, np.inf, -np.inf])
+@pytest.mark.parametrize("pos", [(0, 0, 0, 0), (2, 11, 6, 39), (1, 10, 3, 30), (1, 9, 0, 31),
+                                 (0, 5, 6, 1)], ids=str)
+def test_4d_nan_inf_rejected(hV, bad, pos):
+    """A NaN or an infinity anywhere in a 4D float image (corners, the edges
+    of the 30-voxel x tiles and of the blocks of own z-slices, the last
+    volume) is an error of the whole call; the handle stays usable."""
+    img = synth.grf_f32((3, 12, 7, 40), 1.5, S + 62)
+    good = img.copy()
+    img[pos] = bad
+    with pytest.raises(ecc.EccError) as ei:
+        ecc.ecc_compute(hV, img)
+    assert ei.value.status == ecc.ECC_ERR_VALUE
+    t, chi = ecc.ecc_compute(hV, good)
+    t_ref, chi_ref = oracle.ecc_pairs_float(good, "V")
+    assert np.array_equal(t, t_ref) and np.array_equal(chi, chi_ref)
+
+
+@pytest.mark.parametrize("conv", ["V", "T"])
+def test_4d_signed_zeros(hV, hT, conv):
+    """+0.0 and -0.0 are one value (ties between them broken by the linear
+    index): a 4D field with many zeros of both signs against the oracle."""
+    rng = np.random.default_rng(S + 63)
+    shape = (4, 11, 9, 37)
+    img = rng.choice(np.array([-1.5, -0.0, 0.0, 0.75], np.float32), size=shape)
+    img[0, 0, 0, :8] = -0.0
+    t, chi = ecc.ecc_compute(_handle(hV, hT, conv), img)
+    t_ref, chi_ref = oracle.ecc_pairs_float(img, conv)
+    assert np.array_equal(t, t_ref) and np.array_equal(chi, chi_ref)
+
+
 def test_bad_arguments(hV):
     lib = ecc.load()
     import ctypes as C

@@ -392,6 +392,9 @@ static int err_word_status(ecc_handle* h, int word) {
 // keeps at most kPairBlocks; a block it lets go lives on until its result is
 // released.
 constexpr size_t kPairBlocks = 3;
+// Pair lists up to this size are copied back whole, before their surviving
+// count is known (one wait instead of two).
+constexpr unsigned long long kSpeculativePairBytes = 32ull << 20;
 static ResultBlock* take_pair_block(ecc_handle* h, size_t need) {
   for (ResultBlock* b : h->pair_blocks) {
     // refs == 1: only the handle's reference; no other thread can add one
@@ -472,44 +475,68 @@ static int compute_float(ecc_handle* h, const void* d_img, const Shape& s, ecc_r
   }
   if (e) return cuda_err(h, e, "pairs kernel");
   h->launches += cnt;
-  unsigned long long npairs = 0;
-  if ((e = cudaMemcpyAsync(&npairs, h->pair_count.p, 8, cudaMemcpyDeviceToHost, st)))
+  // the pair count and the error word into pinned memory, one wait
+  if ((e = cudaMemcpyAsync(&h->h_cnt[0], h->pair_count.p, 8, cudaMemcpyDeviceToHost, st)))
     return cuda_err(h, e, "copy count");
   int word = 0;
   int rc = read_err_word(h, st, &word);
   if (rc) return rc;
   if ((rc = err_word_status(h, word))) return rc;
+  const unsigned long long npairs = h->h_cnt[0];
   cnt = 0;
   if ((e = launch_float_tail(h->pairs.as<unsigned long long>(), (int64_t)npairs, h->tmp.p,
                              h->tmp.cap, h->out_vals.as<uint32_t>(), h->out_chi.as<long long>(),
                              h->out_count.as<unsigned long long>(), st, &cnt)))
     return cuda_err(h, e, "float tail");
   h->launches += cnt;
-  unsigned long long k = 0;
-  if ((e = cudaMemcpyAsync(&k, h->out_count.p, 8, cudaMemcpyDeviceToHost, st)))
+  // The result: [header][chi][thresholds] in a pinned block. k <= npairs
+  // pairs survive the reduction; while npairs pairs are at most
+  // kSpeculativePairBytes, all npairs slots are copied together with k
+  // behind one wait, else k is read first.
+  ResultBlock* blk = nullptr;
+  size_t cap_pairs = 0;
+  // a block for cap_pairs pairs, handed to the result at once (its header
+  // written, so that ecc_result_free releases it on any later error)
+  auto take_block = [&]() -> bool {
+    if (!(blk = take_pair_block(h, kResultHeader + 12 * cap_pairs))) return false;
+    uint64_t* hdr = reinterpret_cast<uint64_t*>(blk->p);
+    hdr[0] = reinterpret_cast<uint64_t>(blk);
+    hdr[1] = kResultMagic;
+    out->owned = 2;  // the result's reference to blk; released by ecc_result_free
+    out->chi = reinterpret_cast<int64_t*>(blk->p + kResultHeader);
+    return true;
+  };
+  auto copy_pairs = [&](size_t n) -> cudaError_t {
+    cudaError_t ce = cudaMemcpyAsync(blk->p + kResultHeader, h->out_chi.p, 8 * n,
+                                     cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(blk->p + kResultHeader + 8 * cap_pairs, h->out_vals.p, 4 * n,
+                           cudaMemcpyDeviceToHost, st);
+    return ce;
+  };
+  if ((e = cudaMemcpyAsync(&h->h_cnt[1], h->out_count.p, 8, cudaMemcpyDeviceToHost, st)))
     return cuda_err(h, e, "copy count");
+  if (npairs > 0 && 12 * npairs <= kSpeculativePairBytes) {
+    cap_pairs = (size_t)npairs;
+    if (!take_block()) return set_err(h, ECC_ERR_OOM, "pinned result block");
+    if ((e = copy_pairs(cap_pairs))) return cuda_err(h, e, "copy pairs");
+  }
   if ((rc = sync_stream(h, st))) return rc;
+  const unsigned long long k = h->h_cnt[1];
   out->npairs = (int64_t)k;
-  if (k == 0) {
+  if (k == 0 && !blk) {
     out->thresholds = static_cast<float*>(std::malloc(sizeof(float)));
     out->chi = static_cast<int64_t*>(std::malloc(sizeof(int64_t)));
     if (!out->thresholds || !out->chi) return set_err(h, ECC_ERR_OOM, "host result");
     return ECC_OK;
   }
-  // [header][chi: 8k bytes][thresholds: 4k bytes] in a pinned block
-  const size_t need = kResultHeader + 12 * (size_t)k;
-  ResultBlock* blk = take_pair_block(h, need);
-  if (!blk) return set_err(h, ECC_ERR_OOM, "pinned result block of %zu bytes", need);
-  uint64_t* hdr = reinterpret_cast<uint64_t*>(blk->p);
-  hdr[0] = reinterpret_cast<uint64_t>(blk);
-  hdr[1] = kResultMagic;
-  out->chi = reinterpret_cast<int64_t*>(blk->p + kResultHeader);
-  out->thresholds = reinterpret_cast<float*>(blk->p + kResultHeader + 8 * (size_t)k);
-  out->owned = 2;  // the result's reference to blk; released by ecc_result_free
-  if ((e = cudaMemcpyAsync(out->chi, h->out_chi.p, 8 * k, cudaMemcpyDeviceToHost, st)) ||
-      (e = cudaMemcpyAsync(out->thresholds, h->out_vals.p, 4 * k, cudaMemcpyDeviceToHost, st)))
-    return cuda_err(h, e, "copy pairs");
-  if ((rc = sync_stream(h, st))) return rc;
+  if (!blk) {
+    cap_pairs = (size_t)k;
+    if (!take_block()) return set_err(h, ECC_ERR_OOM, "pinned result block");
+    if ((e = copy_pairs(cap_pairs))) return cuda_err(h, e, "copy pairs");
+    if ((rc = sync_stream(h, st))) return rc;
+  }
+  out->thresholds = reinterpret_cast<float*>(blk->p + kResultHeader + 8 * cap_pairs);
   return ECC_OK;
 }
 
@@ -592,7 +619,8 @@ int ecc_create(const ecc_config* cfg, ecc_handle** out) {
       (e = cudaMemset(h->errw.p, 0, sizeof(int))) ||
       (e = h->done.ensure(sizeof(unsigned int))) ||
       (e = cudaMemset(h->done.p, 0, sizeof(unsigned int))) ||
-      (e = cudaMallocHost(&h->h_err, sizeof(int)))) {
+      (e = cudaMallocHost(&h->h_err, sizeof(int))) ||
+      (e = cudaMallocHost(&h->h_cnt, 2 * sizeof(unsigned long long)))) {
     g_create_err = std::string("CUDA setup: ") + cudaGetErrorString(e);
     ecc_destroy(h);
     return e == cudaErrorMemoryAllocation ? ECC_ERR_OOM : ECC_ERR_CUDA;
@@ -622,6 +650,7 @@ void ecc_destroy(ecc_handle* h) {
   for (ResultBlock* b : h->pair_blocks) result_block_release(b);
   delete h->tuner;
   if (h->h_err) cudaFreeHost(h->h_err);
+  if (h->h_cnt) cudaFreeHost(h->h_cnt);
   if (h->h_curve) cudaFreeHost(h->h_curve);
   for (cudaEvent_t ev : h->up_ev) cudaEventDestroy(ev);
   if (h->sync_ev) cudaEventDestroy(h->sync_ev);

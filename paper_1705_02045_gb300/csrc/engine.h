@@ -111,6 +111,7 @@ struct ecc_handle {
   int64_t clean_bins = 0;               // clean_bins entries (fused launches keep it so)
   ecc::DevBuf batch_desc, batch_items, batch_vcec, batch_curve;
   int* h_err = nullptr;                 // pinned scalar for error readback
+  unsigned long long* h_cnt = nullptr;  // pinned counts of the float path (pairs, survivors)
   std::vector<cudaEvent_t> up_ev;       // chunked host-image upload (ecc_compute)
   cudaEvent_t up_free = nullptr;        // the image buffer's previous readers are done
   cudaEvent_t sync_ev = nullptr;        // bounded waits of the blocking calls

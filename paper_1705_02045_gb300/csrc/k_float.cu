@@ -22,7 +22,7 @@ namespace {
 
 using u64 = unsigned long long;
 
-constexpr int kRThreads = 256, kRItems = 16, kRTile = kRThreads * kRItems;
+constexpr int kRThreads = 256, kRItems = 4, kRTile = kRThreads * kRItems;
 constexpr int kSThreads = 256, kSItems = 8, kSTile = kSThreads * kSItems;
 constexpr int kWarps = kRThreads / 32;
 

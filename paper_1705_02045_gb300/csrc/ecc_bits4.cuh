@@ -15,14 +15,15 @@
 // the same 3D offsets and b+- the straight w neighbours; each G_3 is 13 - N
 // with N the 26-term count of the 3D kernels.
 //
-// Layout: a block of 12 warps holds 12 consecutive z-slices of one 30 x 30
-// (y, x) tile, 10 own slices and the z-collar slice below and above them; a
-// warp holds 32 rows of its slice (lanes 0 and 31 the y-collar) and a lane
-// one 32-voxel word (bits 0 and 31 the x-collar), as in the warp-column
-// layout of the 3D kernel. The block marches along w; the bit planes of every
-// slice's rows in volumes w and w + 1 sit in shared memory (double-buffered
-// by volume parity), rows y +- 1 of a slice come by warp shuffles. The collar
-// warps advance only the borrow chains their own-slice neighbours read.
+// Layout: a block holds 13 consecutive z-slices of one 30 x 30 (y, x) tile,
+// 11 own slices and the z-collar slice below and above them, in 12 warps: a
+// warp per own slice and one for both collar slices. A warp holds 32 rows of
+// a slice (lanes 0 and 31 the y-collar) and a lane one 32-voxel word (bits 0
+// and 31 the x-collar), as in the warp-column layout of the 3D kernel. The
+// block marches along w; the bit planes of every slice's rows in volumes w
+// and w + 1 sit in shared memory (double-buffered by volume parity), rows
+// y +- 1 of a slice come by warp shuffles. The collar warp advances only the
+// borrow chains the own slices next to the collar slices read.
 // Comparison words travel to the later voxel's row through shared memory:
 // those with slice z + 1 within the step, those with volume w + 1 to the next
 // step. Two block barriers per step.
@@ -35,17 +36,14 @@
 
 namespace ecc {
 
-constexpr int k4ZB = 10;            // own z-slices per block
-constexpr int k4Warps = k4ZB + 2;   // one warp per slice, the two collar slices included
+constexpr int k4ZB = 11;             // own z-slices per block
+constexpr int k4Slices = k4ZB + 2;   // with the collar slice below and above
+constexpr int k4Warps = k4ZB + 1;    // a warp per own slice, one for both collar slices
 
-// Slice of warp wi (z = tz * k4ZB - 1 + slice): warps 0 .. k4ZB - 1 hold the
-// own slices 1 .. k4ZB, warp k4ZB the collar slice 0 below them and warp
-// k4ZB + 1 the collar slice above. The SM's four schedulers take warps by
-// index mod 4, so the two lighter collar warps go to two schedulers that
-// otherwise run two own warps each, the other two schedulers three own warps.
-__host__ __device__ constexpr int bits4_slice(int wi) {
-  return wi < k4ZB ? wi + 1 : (wi == k4ZB ? 0 : k4ZB + 1);
-}
+// Slices: z = tz * k4ZB - 1 + slice. Warps 0 .. k4ZB - 1 hold the own slices
+// 1 .. k4ZB, warp k4ZB the collar slices 0 and k4ZB + 1. The SM's four
+// schedulers take warps by index mod 4: three of them run three own warps,
+// the fourth two own warps and the lighter collar warp.
 
 struct Bits4Img {
   const unsigned char* img;  // volume w_mem_lo
@@ -80,7 +78,7 @@ constexpr int k4PairBuf = 64;
 // the in-volume exports to slice z + 1, the cross exports of two steps.
 template <int NB>
 constexpr size_t bits4_smem_words() {
-  return (size_t)2 * k4Warps * NB * 32 + (size_t)k4Warps * 9 * 32 + (size_t)2 * k4Warps * 27 * 32;
+  return (size_t)2 * k4Slices * NB * 32 + (size_t)k4Slices * 9 * 32 + (size_t)2 * k4Slices * 27 * 32;
 }
 
 namespace b4 {
@@ -271,8 +269,9 @@ __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t t
   constexpr int RAW = 8 * EB;
   const unsigned FULL = 0xFFFFFFFFu, ALL = 0xFFFFFFFFu;
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-  const int sl = bits4_slice(wi);
-  const int role = sl == 0 ? 1 : sl == k4ZB + 1 ? 2 : 0;  // own, collar below, collar above
+  const bool collar = wi == k4ZB;  // the warp of both collar slices
+  const int sl = collar ? 0 : wi + 1;  // own slice (the collar warp: slice 0 first)
+  constexpr int kTop = k4ZB + 1;       // the collar slice above
   const int64_t nw = im.n[0], nz = im.n[1], ny = im.n[2], nx = im.n[3];
   const int64_t y = ty * kWcOwn - 1 + lane, x0 = tx * kWcOwn - 1;
   const int64_t z = tz * k4ZB - 1 + sl;
@@ -287,12 +286,12 @@ __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t t
     const int64_t lo = x0 < 0 ? -x0 : 0, hi = nx - x0 >= 32 ? 32 : nx - x0;
     xin = (hi >= 32 ? FULL : ((1u << hi) - 1u)) & (FULL << lo);
   }
-  const bool own = role == 0 && lane >= 1 && lane <= kWcOwn && vy[1] && vz[1];
+  const bool own = !collar && lane >= 1 && lane <= kWcOwn && vy[1] && vz[1];
   const uint32_t dep = own ? (xin & 0x7FFFFFFEu) : 0u;
   const uint32_t xo = ~xin;
   const uint32_t cx[3] = {xo >> 1, xo, xo << 1};
   const size_t row_bytes = (size_t)nx * EB;
-  const int ip = sl + 1 < k4Warps ? sl + 1 : sl, imn = sl > 0 ? sl - 1 : sl;
+  const int ip = sl + 1, imn = sl > 0 ? sl - 1 : sl;
   // k4Pairs: this warp's pair buffer and its fill (the same in every lane)
   unsigned long long* pbuf = reinterpret_cast<unsigned long long*>(hist) + wi * k4PairBuf;
   int pfill = 0;
@@ -312,44 +311,50 @@ __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t t
     pfill = 0;
   };
 
-  uint32_t* SP = sm;                                  // [2][k4Warps][NB][32], by slice
-  uint32_t* GI = SP + 2 * k4Warps * NB * 32;          // [k4Warps][9][32]
-  uint32_t* GC = GI + k4Warps * 9 * 32;               // [2][k4Warps][27][32]
+  uint32_t* SP = sm;                                  // [2][k4Slices][NB][32]
+  uint32_t* GI = SP + 2 * k4Slices * NB * 32;         // [k4Slices][9][32]
+  uint32_t* GC = GI + k4Slices * 9 * 32;              // [2][k4Slices][27][32]
   auto sp_at = [&](int64_t wv, int slice, int k) -> uint32_t* {
-    return SP + (((int)(wv & 1) * k4Warps + slice) * NB + k) * 32;
+    return SP + (((int)(wv & 1) * k4Slices + slice) * NB + k) * 32;
   };
   auto gc_at = [&](int64_t wv, int slice, int dz, int dy, int dx) -> uint32_t* {
-    return GC + (((int)(wv & 1) * k4Warps + slice) * 27 + (dz + 1) * 9 + (dy + 1) * 3 + dx + 1) * 32;
+    return GC + (((int)(wv & 1) * k4Slices + slice) * 27 + (dz + 1) * 9 + (dy + 1) * 3 + dx + 1) * 32;
   };
-  auto row_ptr = [&](int64_t wp) {
-    return im.img + (((size_t)(wp - im.w_mem_lo) * (size_t)nz + (size_t)z) * (size_t)ny +
+  // this lane's row of slice s in volume wp
+  auto row_ptr_s = [&](int s, int64_t wp) {
+    const int64_t zs = tz * k4ZB - 1 + s;
+    return im.img + (((size_t)(wp - im.w_mem_lo) * (size_t)nz + (size_t)zs) * (size_t)ny +
                      (size_t)y) * row_bytes;
   };
-  auto load_raw = [&](int64_t wp, uint32_t* raw) {
-    if (!vy[1] || !vz[1] || wp < 0 || wp >= nw) return;
+  auto row_in = [&](int s, int64_t wp) {
+    const int64_t zs = tz * k4ZB - 1 + s;
+    return vy[1] && zs >= 0 && zs < nz && wp >= 0 && wp < nw;
+  };
+  auto load_raw_s = [&](int s, int64_t wp, uint32_t* raw) {
+    if (!row_in(s, wp)) return;
     if (wp < im.w_mem_lo || wp >= im.w_mem_hi) {
       atomicOr(im.err, kErrOverflow);
       return;
     }
     if constexpr (EB == 4)
-      b4::load_window4(row_ptr(wp), x0, nx, fast, raw);
+      b4::load_window4(row_ptr_s(s, wp), x0, nx, fast, raw);
     else
-      wc::load_window<EB>(row_ptr(wp), x0, nx, fast, raw);
+      wc::load_window<EB>(row_ptr_s(s, wp), x0, nx, fast, raw);
   };
-  // the row's bytes of volume wp into L2 (its first and last byte: at most
-  // 32 voxels + 2, two 128-byte lines for 4-byte values)
-  auto prefetch_row = [&](int64_t wp) {
-    if (!vy[1] || !vz[1] || wp < 0 || wp >= nw || wp < im.w_mem_lo || wp >= im.w_mem_hi) return;
+  // the row's bytes into L2 (its first and last byte: at most 32 voxels + 2,
+  // two 128-byte lines for 4-byte values)
+  auto prefetch_row_s = [&](int s, int64_t wp) {
+    if (!row_in(s, wp) || wp < im.w_mem_lo || wp >= im.w_mem_hi) return;
     const int64_t xa = x0 < 0 ? 0 : x0, xb = (x0 + 32 < nx ? x0 + 32 : nx) - 1;
-    const unsigned char* row = row_ptr(wp);
+    const unsigned char* row = row_ptr_s(s, wp);
     asm volatile("prefetch.global.L2 [%0];" ::"l"(row + xa * EB));
     asm volatile("prefetch.global.L2 [%0];" ::"l"(row + xb * EB));
   };
-  // bit planes of a loaded row; value checks on the voxels inside the image.
-  // Rows outside the image keep whatever planes they get: every comparison
-  // with them is replaced through the outside masks.
-  auto make_planes = [&](int64_t wp, uint32_t* raw, uint32_t* P) {
-    const uint32_t inside = (vy[1] && vz[1] && wp >= 0 && wp < nw) ? xin : 0u;
+  // bit planes of a loaded row of slice s; value checks on the voxels inside
+  // the image. Rows outside the image keep whatever planes they get: every
+  // comparison with them is replaced through the outside masks.
+  auto make_planes_s = [&](int s, int64_t wp, uint32_t* raw, uint32_t* P) {
+    const uint32_t inside = row_in(s, wp) ? xin : 0u;
     if constexpr (EB == 4) {
       // order-preserving keys: -0.0 as +0.0, negative values complemented,
       // the sign bit set on the others
@@ -397,33 +402,42 @@ __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t t
   for (int i = 0; i < RAW; ++i) raw[i] = 0u;
   uint32_t Y[NB];  // planes of the volume loaded ahead
   const int64_t ws = w0 == 0 ? w0 : w0 - 1;
-  load_raw(ws, raw);
-  make_planes(ws, raw, Y);
+  auto prime = [&](int s) {
+    load_raw_s(s, ws, raw);
+    make_planes_s(s, ws, raw, Y);
 #pragma unroll
-  for (int k = 0; k < NB; ++k) sp_at(ws, sl, k)[lane] = Y[k];
-  load_raw(ws + 1, raw);
-  make_planes(ws + 1, raw, Y);
+    for (int k = 0; k < NB; ++k) sp_at(ws, s, k)[lane] = Y[k];
+    load_raw_s(s, ws + 1, raw);
+    make_planes_s(s, ws + 1, raw, Y);
 #pragma unroll
-  for (int k = 0; k < NB; ++k) sp_at(ws + 1, sl, k)[lane] = Y[k];
-  if (w0 == 0) {
-    // no volume below the first: its exports are zero (every neighbour there
-    // is outside, i.e. after)
+    for (int k = 0; k < NB; ++k) sp_at(ws + 1, s, k)[lane] = Y[k];
+    if (w0 == 0) {
+      // no volume below the first: its exports are zero (every neighbour
+      // there is outside, i.e. after)
 #pragma unroll
-    for (int e = 0; e < 27; ++e) GC[(((int)((ws - 1) & 1) * k4Warps + sl) * 27 + e) * 32 + lane] = 0u;
-  }
-  // chains a slice's role does not advance keep these values
+      for (int e = 0; e < 27; ++e) GC[(((int)((ws - 1) & 1) * k4Slices + s) * 27 + e) * 32 + lane] = 0u;
+    }
+  };
+  prime(sl);
+  if (collar) prime(kTop);
+  // chains the collar warp does not advance keep these values
   uint32_t bx = 0u, by[3] = {0u, 0u, 0u}, bz[3][3] = {}, bw[3][3][3] = {};
   __syncthreads();
 
   for (int64_t w = ws; w < w1; ++w) {
     const bool more = w + 2 <= w1;
     // volume w + 2 comes to L2 now and to registers after the comparisons
-    if (more) prefetch_row(w + 2);
+    if (more) {
+      prefetch_row_s(sl, w + 2);
+      if (collar) prefetch_row_s(kTop, w + 2);
+    }
     // ---- the forward comparisons, bit plane by bit plane
     // Each chain starts at 0 (no borrow) and takes the planes LSB first; the
     // plane loop is unrolled only partly, the planes coming from shared memory.
     constexpr int kUnroll = NB % 8 == 0 ? 8 : NB % 7 == 0 ? 7 : 1;
-    auto advance = [&](auto groups) {
+    // sc: the slice whose rows are compared; s_lo, s_hi: the slices below
+    // and above it
+    auto advance = [&](auto groups, int sc, int s_lo, int s_hi) {
       constexpr int G = decltype(groups)::value;
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
@@ -438,7 +452,7 @@ __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t t
       if constexpr ((G & k4GroupC) != 0) bx = 0u;
 #pragma unroll kUnroll
       for (int k = 0; k < NB; ++k) {
-        const uint32_t c = sp_at(w, sl, k)[lane];
+        const uint32_t c = sp_at(w, sc, k)[lane];
         const uint32_t C[3] = {c >> 1, c, c << 1};  // [dx+1]: C[i + 1], C[i], C[i - 1]
         // borrow of n - cc through this plane: [n < cc] over the planes so far
         auto chain = [&](uint32_t& b, uint32_t n, uint32_t cc) {
@@ -452,7 +466,7 @@ __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t t
         };
         if constexpr ((G & k4GroupA) != 0) {
           uint32_t r[3];
-          rows(sp_at(w + 1, imn, k)[lane], r);
+          rows(sp_at(w + 1, s_lo, k)[lane], r);
 #pragma unroll
           for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
@@ -460,8 +474,8 @@ __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t t
         }
         if constexpr ((G & k4GroupB) != 0) {
           uint32_t r[3], q[3];
-          rows(sp_at(w, ip, k)[lane], r);
-          rows(sp_at(w + 1, ip, k)[lane], q);
+          rows(sp_at(w, s_hi, k)[lane], r);
+          rows(sp_at(w + 1, s_hi, k)[lane], q);
 #pragma unroll
           for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
@@ -473,7 +487,7 @@ __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t t
         if constexpr ((G & k4GroupC) != 0) {
           const uint32_t ny1 = __shfl_down_sync(FULL, c, 1);
           uint32_t r[3];
-          rows(sp_at(w + 1, sl, k)[lane], r);
+          rows(sp_at(w + 1, sc, k)[lane], r);
           chain(bx, c, C[2]);
 #pragma unroll
           for (int dx = 0; dx < 3; ++dx) {
@@ -484,13 +498,13 @@ __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t t
         }
       }
     };
-    if (role == 0)
-      advance(std::integral_constant<int, k4GroupA | k4GroupB | k4GroupC>{});
-    else if (role == 1)
-      advance(std::integral_constant<int, k4GroupB>{});
-    else
-      advance(std::integral_constant<int, k4GroupA>{});
-    if (more) load_raw(w + 2, raw);
+    if (!collar) {
+      advance(std::integral_constant<int, k4GroupA | k4GroupB | k4GroupC>{}, sl, imn, ip);
+    } else {
+      advance(std::integral_constant<int, k4GroupB>{}, 0, 0, 1);
+      advance(std::integral_constant<int, k4GroupA>{}, kTop, k4ZB, kTop);
+    }
+    if (more) load_raw_s(sl, w + 2, raw);
     const bool w_in = w >= 0 && w < nw, w1_in = w + 1 >= 0 && w + 1 < nw;
     const bool c_in = vy[1] && vz[1] && w_in;
     const uint32_t co[3] = {c_in ? cx[0] : ALL, c_in ? cx[1] : ALL, c_in ? cx[2] : ALL};
@@ -509,30 +523,48 @@ __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t t
     }
     // ---- exports: to slice z + 1 (this step) and to volume w + 1 (next step),
     // the words some own slice reads
-    if (role != 2) {
 #pragma unroll
-      for (int dy = 0; dy < 3; ++dy)
+    for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-        for (int dx = 0; dx < 3; ++dx) GI[((sl * 9) + dy * 3 + dx) * 32 + lane] = Gz[dy][dx];
-    }
+      for (int dx = 0; dx < 3; ++dx) GI[((sl * 9) + dy * 3 + dx) * 32 + lane] = Gz[dy][dx];
+    if (!collar) {
 #pragma unroll
-    for (int dz = 0; dz < 3; ++dz) {
-      if (role == 0 || (role == 1 && dz == 2) || (role == 2 && dz == 0)) {
+      for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
         for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
           for (int dx = 0; dx < 3; ++dx) gc_at(w, sl, dz - 1, dy - 1, dx - 1)[lane] = Gw[dz][dy][dx];
-      }
+    } else {
+      // slice 0: its words with slice 1 of volume w + 1; the top collar
+      // slice: its words with the slice below it in volume w + 1, under that
+      // slice's own outside masks
+      const int64_t zt = tz * k4ZB - 1 + kTop;
+      const bool vzt0 = zt - 1 >= 0 && zt - 1 < nz, vzt1 = zt >= 0 && zt < nz;
+      const bool ct_in = vy[1] && vzt1 && w_in;
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          gc_at(w, 0, 1, dy - 1, dx - 1)[lane] = Gw[2][dy][dx];
+          gc_at(w, kTop, -1, dy - 1, dx - 1)[lane] =
+              gcmp(bw[0][dy][dx], ct_in ? cx[dx] : ALL, (vy[dy] && vzt0 && w1_in) ? xo : ALL);
+        }
     }
     uint32_t Gydn[3];  // row y - 1's (0, 0, +1, dx) words
 #pragma unroll
     for (int dx = 0; dx < 3; ++dx) Gydn[dx] = __shfl_up_sync(FULL, Gy[dx], 1);
     // the planes of volume w + 2, stored once every warp is done with volume w
-    if (more) make_planes(w + 2, raw, Y);
+    if (more) make_planes_s(sl, w + 2, raw, Y);
+    if (more && collar) load_raw_s(kTop, w + 2, raw);
     __syncthreads();
     if (more) {
 #pragma unroll
       for (int k = 0; k < NB; ++k) sp_at(w + 2, sl, k)[lane] = Y[k];
+      if (collar) {
+        make_planes_s(kTop, w + 2, raw, Y);
+#pragma unroll
+        for (int k = 0; k < NB; ++k) sp_at(w + 2, kTop, k)[lane] = Y[k];
+      }
     }
     // ---- the change evaluation and deposits
     uint32_t nzm = 0u;
@@ -613,7 +645,7 @@ __device__ void bits4_span(const Bits4Img& im, int64_t tx, int64_t ty, int64_t t
       nzm = any & dep;
     }
     // deposits: one voxel per lane and round (the pair append is warp-wide)
-    const unsigned char* rowz = row_ptr(w);
+    const unsigned char* rowz = row_ptr_s(sl, w);
     while (__any_sync(FULL, nzm != 0u)) {
       const bool has = nzm != 0u;
       int j = 0;

@@ -450,7 +450,10 @@ def bench_serving(h, reqs, rate_hz: float, seed: int, borrowed: bool = False, re
         st, curve = ecc.ecc_poll(h, rid, timeout_us=600_000_000)
         assert st == ecc.ECC_OK
         if i % 16 == 0:
-            kept[i] = curve
+            # a copy: a served curve is a view into a pinned result slab of
+            # the library, and a live view keeps the whole slab from reuse
+            kept[i] = np.array(curve)
+        del curve
     wall = time.perf_counter() - t0
     if ref is not None:
         for i, curve in kept.items():

@@ -1325,23 +1325,35 @@ void serve_loop(ecc_handle* h) {
         PinnedSlab* sb = take_records(sv, need, &off);
         lk.unlock();
         int rc = ECC_OK;
-        PinnedSlab* fresh = nullptr;
+        std::vector<PinnedSlab*> fresh;
         if (!sb) {
-          fresh = new PinnedSlab();
-          fresh->blk = new ResultBlock();
-          fresh->blk->cap = std::max(kSlabBytes, (need + 255) & ~size_t(255));
-          if (cudaMallocHost(&fresh->blk->p, fresh->blk->cap) != cudaSuccess) {
-            cudaGetLastError();
-            delete fresh->blk;
-            delete fresh;
-            fresh = nullptr;
-            rc = set_err(h, ECC_ERR_OOM, "pinned result slab");
+          // The pool grows by a quarter (at least one slab): pinning host
+          // memory takes milliseconds and holds up every request behind this
+          // batch, so a pool sized by a first burst keeps headroom for the
+          // different packing of the next one.
+          size_t grow = 1;
+          {
+            std::lock_guard<std::mutex> lk2(sv->mu);
+            grow = std::max<size_t>(1, sv->slabs.size() / 4);
+          }
+          for (size_t i = 0; i < grow; ++i) {
+            PinnedSlab* f = new PinnedSlab();
+            f->blk = new ResultBlock();
+            f->blk->cap = std::max(kSlabBytes, i == 0 ? (need + 255) & ~size_t(255) : 0);
+            if (cudaMallocHost(&f->blk->p, f->blk->cap) != cudaSuccess) {
+              cudaGetLastError();
+              delete f->blk;
+              delete f;
+              if (i == 0) rc = set_err(h, ECC_ERR_OOM, "pinned result slab");
+              break;
+            }
+            fresh.push_back(f);
           }
         }
-        if (fresh) {
+        if (!fresh.empty()) {
           std::lock_guard<std::mutex> lk2(sv->mu);
-          sv->slabs.push_back(fresh);
-          sb = take_records(sv, need, &off);  // fits: the new slab is empty
+          for (PinnedSlab* f : fresh) sv->slabs.push_back(f);
+          sb = take_records(sv, need, &off);  // fits: the first new slab is empty
         }
         if (!rc) rc = slot_run(h, sl, sv->eng.tune, sv->specs[free_slot], nullptr, sb->blk->p + off);
         lk.lock();

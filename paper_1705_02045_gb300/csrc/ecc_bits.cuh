@@ -189,6 +189,51 @@ __device__ __forceinline__ uint32_t gcmp(uint32_t b, uint32_t cout, uint32_t nou
 
 }  // namespace bits
 
+// The deposit of a word with many non-zero changes (noisy data): per-voxel N
+// as bytes by the inverse transpose, the row's raw values re-read (an L2
+// hit) from rp (the word's first voxel; left0 voxels of the row from there),
+// and an unrolled deposit with constant byte offsets. Out of line, so that
+// the common path of smooth data keeps its code small.
+template <int NB, int EB, int HM>
+__device__ __noinline__ void deposit_dense(uint32_t n0, uint32_t n1, uint32_t n2, uint32_t n3,
+                                           uint32_t n4, uint32_t nzm, const unsigned char* rp,
+                                           int64_t left0, int* hist, long long* vcec) {
+  constexpr int RAW = 8 * EB;
+  const uint32_t pn[8] = {n0, n1, n2, n3, n4, 0u, 0u, 0u};
+  uint32_t nbyte[8];
+  bits::untranspose8(pn, nbyte);
+  // two halves of 16 voxels keep fewer raw words live
+#pragma unroll
+  for (int hf = 0; hf < 2; ++hf) {
+    uint32_t rz[RAW / 2];
+    const uintptr_t pa = reinterpret_cast<uintptr_t>(rp) + (uintptr_t)(hf * 16 * EB);
+    const uint32_t* q = reinterpret_cast<const uint32_t*>(pa & ~uintptr_t(3));
+    const uint32_t sh8 = (uint32_t)(pa & 3u) * 8u;
+    uint32_t w[RAW / 2 + 1];
+    const int64_t left = left0 - hf * 16;
+    const int64_t bytes = (left >= 16 ? 16 : (left > 0 ? left : 0)) * EB + (int64_t)(pa & 3u);
+#pragma unroll
+    for (int i = 0; i <= RAW / 2; ++i) w[i] = 4 * i < bytes ? __ldg(q + i) : 0u;
+#pragma unroll
+    for (int i = 0; i < RAW / 2; ++i) rz[i] = __funnelshift_r(w[i], w[i + 1], sh8);
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj) {
+      const int j = hf * 16 + jj;
+      if ((nzm >> j) & 1u) {
+        const int N = (int)((nbyte[j >> 2] >> ((j & 3) * 8)) & 31u);
+        uint32_t v = EB == 1 ? (rz[jj >> 2] >> ((jj & 3) * 8)) & 0xFFu
+                             : (rz[jj >> 1] >> ((jj & 1) * 16)) & 0xFFFFu;
+        v &= (1u << NB) - 1u;
+        if (HM == kBitsSmem)
+          atomicAdd(&hist[v], N - 13);
+        else
+          atomicAdd(reinterpret_cast<unsigned long long*>(vcec) + v,
+                    (unsigned long long)(long long)(N - 13));
+      }
+    }
+  }
+}
+
 // Planes [z0, z1) of the row column (tx, ty) of geometry geo, one image. All
 // threads of the block call it; blockDim.x = 32 * (geo.RB / geo.R). pl/g0/g1
 // are the shared exchange arrays (record strides pl_rec (odd, >= NB + 1), 3,
@@ -510,43 +555,11 @@ __device__ void bits_span(const BitsImg& im, const BitsGeo& geo, int64_t tx, int
                     (unsigned long long)(long long)c);
         }
       };
-      if (NB > 8 && __popc(nzm) >= 8) {
-        // many non-zero changes (noisy data of more than 8 bits): per-voxel N
-        // as bytes by the inverse transpose, the row's raw values re-read (an
-        // L2 hit), and a fully unrolled deposit with constant byte offsets.
-        // Not compiled for 8-bit values: there the one-by-one deposits cost
-        // about as much on noise, and the code alone slowed the kernel on
-        // smooth data by 1.5 %.
-        const uint32_t pn[8] = {n0, n1, n2, n3, n4, 0u, 0u, 0u};
-        uint32_t nbyte[8];
-        untranspose8(pn, nbyte);
+      if (__popc(nzm) >= 8) {
+        // many non-zero changes (noisy data): the unrolled deposit, out of line
         const unsigned char* rp = im.img + ((size_t)(z - im.w_mem_lo) * ny + (size_t)y) * row_bytes +
                                   (size_t)x0 * EB;
-        // two halves of 16 voxels keep fewer raw words live
-#pragma unroll
-        for (int hf = 0; hf < 2; ++hf) {
-          uint32_t rz[RAW / 2];
-          const uintptr_t pa = reinterpret_cast<uintptr_t>(rp) + (uintptr_t)(hf * 16 * EB);
-          const uint32_t* q = reinterpret_cast<const uint32_t*>(pa & ~uintptr_t(3));
-          const uint32_t sh8 = (uint32_t)(pa & 3u) * 8u;
-          uint32_t w[RAW / 2 + 1];
-          const int64_t left = nx - x0 - hf * 16;
-          const int64_t bytes = (left >= 16 ? 16 : (left > 0 ? left : 0)) * EB + (int64_t)(pa & 3u);
-#pragma unroll
-          for (int i = 0; i <= RAW / 2; ++i) w[i] = 4 * i < bytes ? __ldg(q + i) : 0u;
-#pragma unroll
-          for (int i = 0; i < RAW / 2; ++i) rz[i] = __funnelshift_r(w[i], w[i + 1], sh8);
-#pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            const int j = hf * 16 + jj;
-            if ((nzm >> j) & 1u) {
-              const int N = (int)((nbyte[j >> 2] >> ((j & 3) * 8)) & 31u);
-              const uint32_t v = EB == 1 ? (rz[jj >> 2] >> ((jj & 3) * 8)) & 0xFFu
-                                         : (rz[jj >> 1] >> ((jj & 1) * 16)) & 0xFFFFu;
-              deposit(v, N - 13);
-            }
-          }
-        }
+        deposit_dense<NB, EB, HM>(n0, n1, n2, n3, n4, nzm, rp, nx - x0, hist, im.vcec);
         nzm = 0;
       }
       while (nzm) {

@@ -1,9 +1,14 @@
-"""The multi-rank path of bench.py on CPU: two gloo ranks on 127.0.0.1.
+"""Multi-process logic on CPU: gloo ranks on 127.0.0.1.
 
 Nothing in this build uses more than one GPU: under torchrun the benchmark
 runs one independent image per rank (replicas) and reports all ranks' voxels
 over the slowest rank's time. These tests check that reduction with real
-processes, without any GPU."""
+processes, without any GPU, and the sharding scheme of one image over
+processes (Sec. 3 "Parallel Computations" and "Post-Processing"): each rank
+computes the partial VCEC of a range of planes, one int64 all-reduce sums
+them and a prefix sum gives the curve. Here the oracle does each rank's part;
+the library's per-device step, ecc_compute_vcec_chunk, is compared with the
+oracle on the GPU (tests/test_gpu_chunks.py)."""
 import os
 import socket
 import sys
@@ -62,3 +67,45 @@ def test_single_rank_needs_no_process_group():
     import bench
     value, slowest = bench.aggregate(2_000_000, 4.0, 1)
     assert slowest == 4.0 and abs(value - 0.5) < 1e-12
+
+
+def _shard_worker(rank, world, port, q, conv):
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle
+        from paper_1705_02045_gb300 import synth
+        img = synth.smooth_u8((23, 17, 19), 1.5, synth.SEED_BASE + 2300)
+        ncoord = img.shape[0] + 1  # cell coordinates along axis 0: 0 .. n0
+        lo, hi = ncoord * rank // world, ncoord * (rank + 1) // world
+        part = torch.from_numpy(oracle.vcec_int_zrange(img, 256, lo, hi, conv))
+        dist.all_reduce(part)  # one int64[bins] sum over the ranks
+        q.put((rank, oracle.ecc_from_vcec(part.numpy()).tolist()))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("conv", ["V", "T"])
+@pytest.mark.parametrize("world", [2, 3])
+def test_plane_sharding_with_one_allreduce_over_gloo(world, conv):
+    sys.path.insert(0, ROOT)
+    import oracle
+    from paper_1705_02045_gb300 import synth
+    want = oracle.ecc_int(synth.smooth_u8((23, 17, 19), 1.5, synth.SEED_BASE + 2300), 256, conv)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_worker, args=(r, world, port, q, conv))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, curve in out:
+        assert curve == want.tolist()
